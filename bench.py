@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 delta-to-main merge.
+
+One step = one whole column merge (Steps 1(a), 1(b), 2(a), 2(b) of Section 5)
+of one synthetic column through dm_merge_column, with inputs resident in HBM.
+Default workload: 100,000,000 main rows of 8-byte values over a 1,000,000-entry
+dictionary (1% unique), Zipf(1.0) codes at 20 bits; 1,000,000 delta rows with
+30% new values.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   # the CPU oracle, as the reference arm
+
+Multi-GPU (torchrun): every rank merges its own column (independent problems,
+weak scaling); only the timing is reduced across ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+from paper_1109_6885_gb300 import traffic  # noqa: E402
+
+METRIC = "merged tuples/s per column"
+UNIT = "tuples/s"
+
+WORKLOADS = {
+    # 100M-row column, 8-byte values, 1% unique, Zipf(1.0) codes, 1M-row delta, 30% new
+    "column-100M-u64-zipf1-delta1M": dict(n_main=100_000_000, m=1_000_000, w=8, n_delta=1_000_000,
+                                          f_new=0.3, dist="zipf", zipf_s=1.0),
+    # the same with 16-byte keys
+    "column-100M-k16-zipf1-delta1M": dict(n_main=100_000_000, m=1_000_000, w=16,
+                                          n_delta=1_000_000, f_new=0.3, dist="zipf", zipf_s=1.0),
+    # 1M-row column over 100k uniform uint64 values at 17 bits, 10k-row delta, half new
+    "column-1M-u64-delta10k": dict(n_main=1_000_000, m=100_000, w=8, n_delta=10_000, f_new=0.5,
+                                   dist="uniform", pool=0),
+}
+DEFAULT_WORKLOAD = "column-100M-u64-zipf1-delta1M"
+L2_BYTES = 129 * 2**20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_column(name: str, rank: int):
+    spec = synth.ColumnSpec(**WORKLOADS[name], seed=synth.column_seed(2, rank))
+    return synth.make_column(spec)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int, enabled: bool):
+        self.proc = None
+        self.path = None
+        if not enabled:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_rate(col, budget_s: float = 20.0):
+    """The oracle as it stands, one host core: tuples/s over whole-column merges."""
+    import oracle
+    n = col.n_main + col.n_delta
+    done, t0 = 0, time.perf_counter()
+    while True:
+        oracle.merge_synth_column(col)
+        done += 1
+        el = time.perf_counter() - t0
+        if el > budget_s / 2 or done >= 3:
+            break
+    return n * done / el, done, el
+
+
+def sample_column(col, rows: int):
+    """The first `rows` main rows with the whole dictionaries and delta."""
+    if rows >= col.n_main:
+        return col
+    codes = col.main_codes[:rows]
+    spec = synth.ColumnSpec(**{**col.spec.__dict__, "n_main": rows})
+    return synth.Column(spec, col.main_dict, codes, col.main_bits, synth.pack(codes, col.main_bits),
+                        col.delta_dict, col.delta_codes)
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build_native()
+    col = make_column(args.workload, 0)
+    rows = col.n_main
+    samp = sample_column(col, rows)
+    n = samp.n_main + samp.n_delta
+    for _ in range(args.warmup):
+        oracle.merge_synth_column(samp)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.merge_synth_column(samp)
+    el = time.perf_counter() - t0
+    value = n * args.steps / el
+    desc = (f"the whole workload per step: {rows:,} main rows, {col.n_delta:,} delta rows, "
+            "one host thread")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"u{8 * col.w}" if col.w < 16 else "u128", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+
+    from paper_1109_6885_gb300 import build
+    from paper_1109_6885_gb300 import dmerge as dm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    dm.load()
+
+    col = make_column(args.workload, rank)
+    m, d, w = col.main_dict.shape[0], col.delta_dict.shape[0], col.w
+    n_tuples = col.n_main + col.n_delta
+    ctx = dm.Context(local)
+    dcol = dm.DeviceColumn.from_numpy(w, col.main_dict, col.main_packed, col.main_bits, col.n_main,
+                                      col.delta_dict, col.delta_codes)
+    res = dm.alloc_result(dcol)
+    ctx.reserve(dm.dm_scratch_bytes(dcol.cin()))
+    cin, cout = dcol.cin(), res.cout()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also checks the result once against the status word)
+    for _ in range(max(args.warmup, 3)):
+        dm.dm_merge_column(ctx, cin, cout, stream)
+    torch.cuda.synchronize()
+    st = ctx.sync_status()
+    if st != dm.DM_OK:
+        raise RuntimeError(f"device status {st} after warm-up")
+    u, b_new = res.u_bits()
+
+    # timed region: K whole merges, CUDA events on the launching stream
+    sampler = ClockSampler(local, not args.no_clocks)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches0 = ctx.launches
+    ctx.timing_sum()
+    barrier()
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        dm.dm_merge_column(ctx, cin, cout, stream, dm.DM_FLAG_TIMING)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    launches = ctx.launches - launches0
+    per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    phase_ms, calls = ctx.timing_sum()
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * n_tuples * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (Step 2(b) re-encode), bytes it must move
+    reencode_ms = phase_ms[2] / max(calls, 1)
+    step2 = traffic.step2_bytes(col.main_bits, b_new, col.n_main, col.n_delta, m, d)
+    peak, peak_kind = measured_peaks()
+    achieved = step2 / (reencode_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "reencode_kernel<b>",
+                "algorithmic_bytes": step2, "peak_source": peak_kind,
+                "phase_ms_avg": {"sort_1a": phase_ms[0] / max(calls, 1),
+                                 "merge_1b_2a": phase_ms[1] / max(calls, 1),
+                                 "reencode_2b": reencode_ms,
+                                 "whole": phase_ms[3] / max(calls, 1)}}
+    step1 = traffic.step1_bytes(w, m, d, u)
+
+    # end to end: host buffers through dm_merge_column_host (pinned memory)
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(dm, ctx, col, m, d, w, u, b_new, args, world, barrier)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, reps, el = cpu_oracle_rate(col)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{reps} whole-column merge(s) of this workload, {el:.1f} s, one thread"}
+
+    if rank == 0:
+        ps = sorted(per_step)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"u{8 * w}" if w < 16 else "u128", "data": "synthetic",
+            "config": {
+                "workload": args.workload, "n_main": col.n_main, "dict_main": m, "value_bytes": w,
+                "bits_in": col.main_bits, "n_delta": col.n_delta, "dict_delta": d, "dict_new": u,
+                "bits_out": b_new, "code_dist": col.spec.dist, "zipf_s": col.spec.zipf_s,
+                "f_new": col.spec.f_new, "l2": (
+                    "inputs larger than L2: each step streams "
+                    f"{(dm.dm_packed_bytes(col.n_main, col.main_bits) + dm.dm_packed_bytes(n_tuples, b_new)) / 1e6:.0f} MB"
+                    f" of packed codes against a {L2_BYTES / 2**20:.0f} MiB L2"),
+                "parallelism": f"{world} independent column(s), one per GPU",
+                "algorithmic_bytes_per_step": step1 + step2,
+            },
+            "latency_ms": {"p50": ps[len(ps) // 2], "p99": ps[min(len(ps) - 1, int(0.99 * len(ps)))],
+                           "min": ps[0], "max": ps[-1]},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(dm, ctx, col, m, d, w, u, b_new, args, world, barrier):
+    import torch
+    kd = dm.key_np_dtype(w)
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a).view(np.int64 if a.dtype == np.uint64 else np.int32)
+                             if a.size else np.zeros(1, np.int32)).pin_memory()
+        return t
+
+    h_md, h_mp = pinned(col.main_dict), pinned(col.main_packed)
+    h_dd, h_dc = pinned(col.delta_dict), pinned(col.delta_codes)
+    n_out = col.n_main + col.n_delta
+    h_new = torch.empty(max((m + d) * (w // 4), 1), dtype=torch.int32).pin_memory()
+    h_packed = torch.empty(max(dm.dm_packed_bytes(n_out, dm.dm_bits_for(m + d)) // 4, 1),
+                           dtype=torch.int32).pin_memory()
+    cin = dm.ColumnIn(w, h_md.data_ptr(), m, h_mp.data_ptr(), col.main_bits, col.n_main,
+                      h_dd.data_ptr(), d, h_dc.data_ptr(), col.n_delta)
+    cout = dm.ColumnOut(h_new.data_ptr(), h_packed.data_ptr(), None, None, None, None)
+    ctx.reserve(dm.dm_host_scratch_bytes(cin))
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        dm.dm_merge_column_host(ctx, cin, cout, stream)
+    steps = args.steps
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        uu, bb = dm.dm_merge_column_host(ctx, cin, cout, stream)
+    torch.cuda.synchronize()
+    barrier()
+    el = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([el], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        el = float(t.item())
+    assert (uu, bb) == (u, b_new)
+    h2d = m * w + col.main_packed.nbytes + d * w + col.delta_codes.nbytes
+    d2h = u * w + dm.dm_packed_bytes(n_out, b_new) + 16
+    return {"value": world * n_out * steps / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * el / steps,
+            "path": "dm_merge_column_host: pinned host inputs -> device, merge, results -> host"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

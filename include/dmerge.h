@@ -1,0 +1,205 @@
+/*
+ * dmerge.h — C ABI of the GB300 delta-to-main merge (libdmerge.so).
+ *
+ * One column merge (Krueger et al., "Fast Updates on Read-Optimized
+ * Databases Using Multi-Core CPUs", Section 5) combines
+ *   - the main partition: a sorted, duplicate-free dictionary U_M and the
+ *     vector M of N_M codes into it, bit-packed at E_C bits, and
+ *   - the delta partition: N_D rows, stored as an insertion-order
+ *     dictionary D_dict of the distinct delta values plus one uint32 code
+ *     per row into D_dict,
+ * into a new dictionary U' = sorted(U_M ∪ D_dict) without duplicates (Eq. 3)
+ * and a new packed vector of N'_M = N_M + N_D codes (Eq. 2): the main rows
+ * in order, then the delta rows in order, each holding the position of its
+ * value in U', at E'_C = ceil(log2 |U'|) bits (Eq. 4).  The translation
+ * tables X_M (old main code -> new code) and X_D (delta code -> new code)
+ * of Section 5.3 are outputs too.
+ *
+ * Steps, each a set of sm_103a kernels:
+ *   1(a)  sort D_dict                 -> U_D, perm   (LSD radix sort)
+ *   1(b)  merge U_M with U_D, dedup   -> U', X_M, X_D (merge path + scan)
+ *   2(a)  E'_C = ceil(log2 |U'|)      -> device scalar
+ *   2(b)  re-encode M and D           -> new packed vector (Eq. 11)
+ *
+ * Formats (the paper fixes none; these are this library's):
+ *   keys      unsigned integers of value_bytes = 4 (uint32), 8 (uint64) or
+ *             16 ({uint64 hi; uint64 lo;}, hi first in memory, compared
+ *             hi first).  Arrays aligned to value_bytes.
+ *   packed    code i occupies stream bits [i*b, (i+1)*b), least significant
+ *             bit first; stream bit k is bit k%32 of little-endian 32-bit
+ *             word k/32.  A stream of n codes at b bits occupies
+ *             dm_packed_bytes(n, b) bytes (a whole number of 16-byte units,
+ *             zero after the last code).  Packed buffers are 16-byte aligned.
+ *   b = 0     legal when the dictionary has at most one entry: every code
+ *             is 0 and the stream has zero bytes.
+ *   duplicates inside D_dict are tolerated: every copy maps to the value's
+ *             single code in U'.  Dictionary entries no row references are
+ *             kept (U' is the union of the dictionaries, Eq. 3).
+ *
+ * Conventions:
+ *   - Every call is asynchronous on the given CUDA stream (a cudaStream_t
+ *     passed as void*; NULL = the legacy default stream) unless it says
+ *     otherwise.  Argument errors are returned immediately, before any
+ *     launch.  Data-dependent errors (U_M not increasing, a code out of
+ *     range, a wait that timed out) are recorded in a per-context device
+ *     status word and returned by dm_sync_status.  Kernels never fault on
+ *     such data: out-of-range codes are clamped and flagged.
+ *   - Inputs are never written.  All pointers in dm_column_in /
+ *     dm_column_out are device pointers owned by the caller; the library
+ *     never frees them.  Scratch memory comes from the context's arena,
+ *     sized at dm_create / dm_reserve; too small an arena returns DM_ENOMEM
+ *     before any launch.
+ *   - A context serves one stream at a time: calls on different streams
+ *     that may overlap need different contexts.
+ */
+#ifndef DMERGE_H_
+#define DMERGE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DM_OK = 0,
+  DM_EINVAL = 1,     /* bad argument: width, size, alignment, NULL */
+  DM_ENOMEM = 2,     /* the context's arena is too small (or allocation failed) */
+  DM_EUNSORTED = 3,  /* U_M is not strictly increasing */
+  DM_ECODE = 4,      /* a main code >= |U_M| or a delta code >= |D_dict| */
+  DM_ECUDA = 5,      /* a CUDA runtime call failed */
+  DM_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
+  DM_EBUSY = 7       /* the request cannot be admitted now */
+} dm_status;
+
+/* flags for dm_merge_column / dm_merge_table */
+#define DM_FLAG_GENERIC_REENCODE 0x1u  /* force the runtime-width Step 2(b) path */
+#define DM_FLAG_X_SMEM 0x2u            /* stage X_M in shared memory (when it fits) */
+#define DM_FLAG_X_GLOBAL 0x4u          /* never stage X_M in shared memory */
+#define DM_FLAG_TIMING 0x8u            /* record per-step CUDA events (dm_last_timing) */
+
+typedef struct dm_ctx dm_ctx;
+
+/* Create a context on `device` with a scratch arena of arena_bytes (may be
+ * 0; grow it later with dm_reserve).  Synchronous. */
+dm_status dm_create(dm_ctx** ctx, int device, size_t arena_bytes);
+void dm_destroy(dm_ctx* ctx);
+/* Grow the arena to at least arena_bytes.  Synchronises the device. */
+dm_status dm_reserve(dm_ctx* ctx, size_t arena_bytes);
+size_t dm_arena_bytes(const dm_ctx* ctx);
+
+/* One column's inputs (device pointers, read only). */
+typedef struct {
+  uint32_t value_bytes;        /* E: 4, 8 or 16 */
+  const void* main_dict;       /* U_M, main_dict_len keys, strictly increasing */
+  uint64_t main_dict_len;      /* |U_M| */
+  const void* main_packed;     /* M: main_rows codes at main_bits bits */
+  uint32_t main_bits;          /* E_C, 0..32, >= dm_bits_for(main_dict_len) */
+  uint64_t main_rows;          /* N_M */
+  const void* delta_dict;      /* D_dict, delta_dict_len keys, insertion order */
+  uint64_t delta_dict_len;     /* |D_dict| (< 2^30) */
+  const uint32_t* delta_codes; /* delta_rows codes, each < delta_dict_len */
+  uint64_t delta_rows;         /* N_D */
+} dm_column_in;
+
+/* One column's outputs (caller-allocated device buffers). */
+typedef struct {
+  void* new_dict;              /* U': capacity main_dict_len + delta_dict_len keys */
+  void* new_packed;            /* dm_packed_bytes(main_rows + delta_rows, dm_max_bits(in)) bytes */
+  uint32_t* x_main;            /* X_M: main_dict_len entries, or NULL (kept in scratch) */
+  uint32_t* x_delta;           /* X_D by insertion code: delta_dict_len entries, or NULL */
+  uint64_t* d_new_dict_len;    /* device scalar: |U'| */
+  uint32_t* d_new_bits;        /* device scalar: E'_C */
+} dm_column_out;
+
+/* Bytes of a packed stream of `rows` codes at `bits` bits (16-byte units). */
+size_t dm_packed_bytes(uint64_t rows, uint32_t bits);
+/* Eq. 4 on the host: ceil(log2 n), 0 for n <= 1. */
+uint32_t dm_bits_for(uint64_t n);
+/* Upper bound of E'_C: dm_bits_for(main_dict_len + delta_dict_len). */
+uint32_t dm_max_bits(const dm_column_in* in);
+/* Arena bytes one dm_merge_column call on `in` needs. */
+size_t dm_scratch_bytes(const dm_column_in* in, uint32_t flags);
+
+/* The whole column merge, Steps 1(a) to 2(b) (Section 5 with the Section
+ * 5.3 translation tables).  Writes out->new_dict[0..|U'|), x_main, x_delta,
+ * the packed vector (dm_packed_bytes(N_M + N_D, E'_C) bytes of it; the
+ * rest of the buffer is not touched), *d_new_dict_len and *d_new_bits.
+ * Asynchronous; no host synchronisation inside. */
+dm_status dm_merge_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out,
+                          void* stream, uint32_t flags);
+
+/* Merge ncols columns of one table (Section 6.2.1 scheme (i): columns are
+ * independent tasks).  Same contract as dm_merge_column per column; the
+ * arena must hold dm_table_scratch_bytes. */
+dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols,
+                         const dm_column_out* out, void* stream, uint32_t flags);
+size_t dm_table_scratch_bytes(const dm_column_in* in, uint32_t ncols, uint32_t flags);
+
+/* The same merge with HOST buffers: every pointer in `in` and `out` is host
+ * memory (page-locked for full copy speed), except that d_new_dict_len and
+ * d_new_bits are ignored and the results go to *new_dict_len / *new_bits.
+ * Inputs are copied to device scratch, merged, and the outputs copied back;
+ * returns after the copies finish (synchronous).  The arena must hold
+ * dm_host_scratch_bytes. */
+dm_status dm_merge_column_host(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out,
+                               void* stream, uint32_t flags, uint64_t* new_dict_len,
+                               uint32_t* new_bits);
+size_t dm_host_scratch_bytes(const dm_column_in* in, uint32_t flags);
+
+/* ---- single steps (same formats; for step-level testing and reuse) ---- */
+
+/* Step 1(a) (Section 5.1 with the Section 5.3 tuple-id map): sort the d
+ * keys of delta_dict; ud_out receives them in increasing order (equal keys
+ * in insertion order) and perm_out[j] the insertion code of ud_out[j]. */
+dm_status dm_sort_delta(dm_ctx* ctx, uint32_t value_bytes, const void* delta_dict, uint64_t d,
+                        void* ud_out, uint32_t* perm_out, void* stream);
+
+/* Step 1(b) + 2(a) (Section 5.1 / 5.3, Eq. 4): merge the sorted U_M (m
+ * keys) and U_D (d keys, perm from Step 1(a)) into U' without duplicates;
+ * x_main[i] / x_delta[perm[j]] receive the U' position of U_M[i] / U_D[j];
+ * *d_u and *d_bits (device scalars) receive |U'| and E'_C. */
+dm_status dm_merge_dicts(dm_ctx* ctx, uint32_t value_bytes, const void* main_dict, uint64_t m,
+                         const void* ud, const uint32_t* perm, uint64_t d, void* new_dict,
+                         uint32_t* x_main, uint32_t* x_delta, uint64_t* d_u, uint32_t* d_bits,
+                         void* stream);
+
+/* Step 2(b) (Section 5.3, Eq. 11): out code i = x_main[M[i]] for i < n_main,
+ * out code n_main + r = x_delta[delta_codes[r]], packed at the width read
+ * from the device scalar *d_bits (which must be <= max_bits; the output
+ * buffer holds dm_packed_bytes(n_main + n_delta, max_bits) bytes).  Table
+ * entries must be < 2^(*d_bits). */
+dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bits,
+                      uint64_t n_main, const uint32_t* delta_codes, uint64_t n_delta,
+                      const uint32_t* x_main, uint64_t m, const uint32_t* x_delta, uint64_t d,
+                      const uint32_t* d_bits, uint32_t max_bits, uint32_t* out_packed,
+                      void* stream, uint32_t flags);
+
+/* ---- status, timing, introspection ---- */
+
+/* Wait for `stream`, read and clear the context's device status word:
+ * DM_OK, or the most severe of DM_ETIMEOUT, DM_EUNSORTED, DM_ECODE. */
+dm_status dm_sync_status(dm_ctx* ctx, void* stream);
+
+/* Milliseconds of Steps 1(a), 1(b)+2(a), 2(b) and the whole merge of the
+ * last dm_merge_column issued with DM_FLAG_TIMING (CUDA events on the
+ * call's stream).  Synchronises on those events. */
+dm_status dm_last_timing(dm_ctx* ctx, float ms[4]);
+
+/* Sum of the per-step milliseconds (as in dm_last_timing) over every
+ * dm_merge_column call issued with DM_FLAG_TIMING since the previous
+ * dm_timing_sum (at most 1024 calls are kept; *calls receives how many were
+ * summed), then forget them.  Synchronises on those events. */
+dm_status dm_timing_sum(dm_ctx* ctx, float ms[4], uint32_t* calls);
+
+/* Kernels this context has launched so far. */
+uint64_t dm_launch_count(const dm_ctx* ctx);
+
+/* Name of a status code. */
+const char* dm_status_str(dm_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMERGE_H_ */

@@ -1,0 +1,612 @@
+// C ABI of libdmerge: context and scratch arena, argument checks, and the
+// entry points declared in include/dmerge.h.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "../../include/dmerge.h"
+#include "dm_common.cuh"
+#include "dm_internal.h"
+
+struct dm_ctx {
+  int device = 0;
+  uint32_t sm_count = 0;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  uint32_t* status = nullptr;      // device status word
+  uint32_t* host_status = nullptr; // pinned readback
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_done = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  bool timing_valid = false;
+  // ring of per-call event quadruples for dm_timing_sum
+  static constexpr uint32_t kRing = 1024;
+  cudaEvent_t* ring = nullptr;
+  uint32_t ring_n = 0;
+  cudaEvent_t* last_ev = nullptr;   // quadruple of the last timed call
+  uint64_t launches = 0;
+};
+
+namespace {
+
+using dm::bits_for;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+bool width_ok(uint32_t w) { return w == 4 || w == 8 || w == 16; }
+
+// Bump allocator over the arena (or a dry run that only sums sizes).
+struct Carver {
+  char* base;
+  size_t used = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  void* take(size_t bytes) {
+    void* p = base ? base + used : nullptr;
+    used += align_up(bytes ? bytes : 1);
+    return p;
+  }
+};
+
+struct ColumnScratch {
+  uint32_t* zero = nullptr;   // one memset covers sort + merge bookkeeping
+  size_t zero_bytes = 0;
+  dm::SortArgs sort{};
+  dm::MergeArgs merge{};
+  uint32_t* xm = nullptr;
+  uint32_t* xd = nullptr;
+  void** slots = nullptr;
+};
+
+// Lay out the scratch of one column merge; with base == nullptr only sizes.
+size_t carve_column(void* base, const dm_column_in* in, const dm_column_out* out, ColumnScratch* cs) {
+  Carver c(base);
+  const uint32_t w = in->value_bytes;
+  const uint64_t m = in->main_dict_len, d = in->delta_dict_len;
+  const uint64_t sort_words = d ? dm::sort_zeroed_words(w, d) : 0;
+  const uint32_t mtiles = dm::merge_tiles(m + d);
+  // zeroed bookkeeping: merge look-back words + tile counter, then the sort's
+  // histograms, tile counters and look-back words
+  const size_t merge_bytes = (size_t)mtiles * 8 + 8;
+  const size_t zero_bytes = merge_bytes + sort_words * 4;
+  char* zero = static_cast<char*>(c.take(zero_bytes));
+  void* k0 = c.take(d * w);
+  void* k1 = c.take(d * w);
+  void* v0 = c.take(d * 4);
+  void* v1 = c.take(d * 4);
+  void* slots = c.take(2 * sizeof(void*));
+  void* xm = (out && out->x_main) ? nullptr : c.take(m * 4);
+  void* xd = (out && out->x_delta) ? nullptr : c.take(d * 4);
+  if (cs && base) {
+    cs->zero = reinterpret_cast<uint32_t*>(zero);
+    cs->zero_bytes = zero_bytes;
+    cs->slots = static_cast<void**>(slots);
+    cs->merge.lookback = reinterpret_cast<uint64_t*>(zero);
+    cs->merge.counter = reinterpret_cast<uint32_t*>(zero + (size_t)mtiles * 8);
+    cs->merge.ntiles = mtiles;
+    uint32_t* zw = reinterpret_cast<uint32_t*>(zero + merge_bytes);
+    cs->sort.in_keys = in->delta_dict;
+    cs->sort.d = d;
+    cs->sort.keys[0] = k0;
+    cs->sort.keys[1] = k1;
+    cs->sort.vals[0] = static_cast<uint32_t*>(v0);
+    cs->sort.vals[1] = static_cast<uint32_t*>(v1);
+    cs->sort.hist = zw;
+    cs->sort.counters = zw + (size_t)w * 256;
+    cs->sort.lookback = zw + (size_t)w * 256 + w;
+    cs->sort.ntiles = dm::sort_tiles(d);
+    cs->sort.final_slot = cs->slots;
+    cs->xm = (out && out->x_main) ? out->x_main : static_cast<uint32_t*>(xm);
+    cs->xd = (out && out->x_delta) ? out->x_delta : static_cast<uint32_t*>(xd);
+  }
+  return c.used;
+}
+
+dm_status check_column(const dm_column_in* in, const dm_column_out* out, bool device_ptrs) {
+  if (!in || !out) return DM_EINVAL;
+  const uint32_t w = in->value_bytes;
+  const uint64_t m = in->main_dict_len, d = in->delta_dict_len;
+  if (!width_ok(w) || in->main_bits > 32) return DM_EINVAL;
+  if (m + d > (1ull << 32) || m > 0xFFFFFFFFull || d >= (1ull << 30)) return DM_EINVAL;
+  if (in->main_bits < bits_for(m)) return DM_EINVAL;
+  if ((in->main_rows && !m) || (in->delta_rows && !d)) return DM_EINVAL;
+  if (in->main_rows + in->delta_rows >= (1ull << 40)) return DM_EINVAL;
+  const size_t ka = w == 16 ? 16 : w;
+  if (m && (!in->main_dict || !aligned(in->main_dict, ka))) return DM_EINVAL;
+  if (d && (!in->delta_dict || !aligned(in->delta_dict, ka))) return DM_EINVAL;
+  if (in->main_rows && in->main_bits && (!in->main_packed || (device_ptrs && !aligned(in->main_packed, 16))))
+    return DM_EINVAL;
+  if (in->delta_rows && (!in->delta_codes || !aligned(in->delta_codes, 4))) return DM_EINVAL;
+  const uint32_t maxb = bits_for(m + d);
+  if (m + d && (!out->new_dict || !aligned(out->new_dict, ka))) return DM_EINVAL;
+  if (in->main_rows + in->delta_rows && maxb &&
+      (!out->new_packed || (device_ptrs && !aligned(out->new_packed, 16))))
+    return DM_EINVAL;
+  if (device_ptrs && (!out->d_new_dict_len || !out->d_new_bits)) return DM_EINVAL;
+  if (out->x_main && !aligned(out->x_main, 4)) return DM_EINVAL;
+  if (out->x_delta && !aligned(out->x_delta, 4)) return DM_EINVAL;
+  return DM_OK;
+}
+
+dm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DM_OK : DM_ECUDA; }
+
+// Steps 1(a)..2(b) of one column whose scratch is laid out at `base`.
+// ev: four events recorded before Step 1(a), before 1(b), before 2(b) and at
+// the end (nullptr: no timing).
+dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* base,
+                     cudaStream_t s, uint32_t flags, cudaEvent_t* ev) {
+  const bool timing = ev != nullptr;
+  ColumnScratch cs;
+  carve_column(base, in, out, &cs);
+  const uint32_t w = in->value_bytes;
+  const uint64_t m = in->main_dict_len, d = in->delta_dict_len;
+  const uint64_t n_out = in->main_rows + in->delta_rows;
+  cudaError_t e = cudaMemsetAsync(cs.zero, 0, cs.zero_bytes, s);
+  if (e != cudaSuccess) return DM_ECUDA;
+  if (timing) cudaEventRecord(ev[0], s);
+  if (d) {
+    cs.sort.status = ctx->status;
+    e = dm::launch_sort(w, cs.sort, s, ctx->sm_count, &ctx->launches);
+    if (e != cudaSuccess) return DM_ECUDA;
+  }
+  if (timing) cudaEventRecord(ev[1], s);
+  if (m + d) {
+    dm::MergeArgs& ma = cs.merge;
+    ma.a = in->main_dict;
+    ma.m = m;
+    ma.b = nullptr;
+    ma.perm = nullptr;
+    ma.b_slot = d ? cs.slots : nullptr;
+    ma.d = d;
+    ma.unew = out->new_dict;
+    ma.xm = cs.xm;
+    ma.xd = cs.xd;
+    ma.d_u = out->d_new_dict_len;
+    ma.d_bits = out->d_new_bits;
+    ma.status = ctx->status;
+    e = dm::launch_merge(w, ma, s, &ctx->launches);
+  } else {
+    e = cudaMemsetAsync(out->d_new_dict_len, 0, sizeof(uint64_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(out->d_new_bits, 0, sizeof(uint32_t), s);
+  }
+  if (e != cudaSuccess) return DM_ECUDA;
+  if (timing) cudaEventRecord(ev[2], s);
+  if (n_out) {
+    dm::ReencodeArgs ra;
+    ra.main_words = static_cast<const uint32_t*>(in->main_packed);
+    ra.main_words_n = dm_packed_bytes(in->main_rows, in->main_bits) / 4;
+    ra.n_main = in->main_rows;
+    ra.dcodes = in->delta_codes;
+    ra.n_delta = in->delta_rows;
+    ra.xm = cs.xm;
+    ra.m = (uint32_t)std::min<uint64_t>(m, 0xFFFFFFFFu);
+    ra.xd = cs.xd;
+    ra.d = (uint32_t)d;
+    ra.d_bits = out->d_new_bits;
+    ra.max_bits = bits_for(m + d);
+    ra.out_words = static_cast<uint32_t*>(out->new_packed);
+    ra.status = ctx->status;
+    e = dm::launch_reencode(in->main_bits, ra, s, ctx->sm_count, flags, &ctx->launches);
+    if (e != cudaSuccess) return DM_ECUDA;
+  }
+  if (timing) cudaEventRecord(ev[3], s);
+  return DM_OK;
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+extern "C" {
+
+const char* dm_status_str(dm_status s) {
+  switch (s) {
+    case DM_OK: return "DM_OK";
+    case DM_EINVAL: return "DM_EINVAL";
+    case DM_ENOMEM: return "DM_ENOMEM";
+    case DM_EUNSORTED: return "DM_EUNSORTED";
+    case DM_ECODE: return "DM_ECODE";
+    case DM_ECUDA: return "DM_ECUDA";
+    case DM_ETIMEOUT: return "DM_ETIMEOUT";
+    case DM_EBUSY: return "DM_EBUSY";
+  }
+  return "DM_UNKNOWN";
+}
+
+size_t dm_packed_bytes(uint64_t rows, uint32_t bits) { return (size_t)((rows * bits + 127) / 128) * 16; }
+
+uint32_t dm_bits_for(uint64_t n) { return bits_for(n); }
+
+uint32_t dm_max_bits(const dm_column_in* in) {
+  return in ? bits_for(in->main_dict_len + in->delta_dict_len) : 0;
+}
+
+size_t dm_scratch_bytes(const dm_column_in* in, uint32_t) {
+  if (!in) return 0;
+  return carve_column(nullptr, in, nullptr, nullptr);
+}
+
+size_t dm_table_scratch_bytes(const dm_column_in* in, uint32_t ncols, uint32_t flags) {
+  size_t mx = 0;
+  for (uint32_t c = 0; c < ncols; ++c) mx = std::max(mx, dm_scratch_bytes(&in[c], flags));
+  return mx;
+}
+
+dm_status dm_create(dm_ctx** out, int device, size_t arena_bytes) {
+  if (!out) return DM_EINVAL;
+  *out = nullptr;
+  dm_ctx* ctx = new (std::nothrow) dm_ctx();
+  if (!ctx) return DM_ENOMEM;
+  ctx->device = device;
+  int sms = 0;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete ctx;
+    return DM_ECUDA;
+  }
+  ctx->sm_count = (uint32_t)sms;
+  if (cudaMalloc(&ctx->status, 256) != cudaSuccess) {
+    delete ctx;
+    return DM_ENOMEM;
+  }
+  cudaMemset(ctx->status, 0, 256);
+  if (cudaMallocHost(&ctx->host_status, sizeof(uint32_t)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming) != cudaSuccess) {
+    dm_destroy(ctx);
+    return DM_ECUDA;
+  }
+  for (auto& e : ctx->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      dm_destroy(ctx);
+      return DM_ECUDA;
+    }
+  }
+  if (arena_bytes) {
+    dm_status st = dm_reserve(ctx, arena_bytes);
+    if (st != DM_OK) {
+      dm_destroy(ctx);
+      return st;
+    }
+  }
+  *out = ctx;
+  return DM_OK;
+}
+
+void dm_destroy(dm_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->status) cudaFree(ctx->status);
+  if (ctx->host_status) cudaFreeHost(ctx->host_status);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
+  for (auto e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->ring) {
+    for (uint32_t i = 0; i < 4 * dm_ctx::kRing; ++i)
+      if (ctx->ring[i]) cudaEventDestroy(ctx->ring[i]);
+    delete[] ctx->ring;
+  }
+  delete ctx;
+}
+
+dm_status dm_reserve(dm_ctx* ctx, size_t bytes) {
+  if (!ctx) return DM_EINVAL;
+  if (bytes <= ctx->arena_bytes) return DM_OK;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return DM_ECUDA;
+  if (ctx->arena) cudaFree(ctx->arena);
+  ctx->arena = nullptr;
+  ctx->arena_bytes = 0;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return DM_ENOMEM;
+  }
+  ctx->arena = p;
+  ctx->arena_bytes = bytes;
+  return DM_OK;
+}
+
+size_t dm_arena_bytes(const dm_ctx* ctx) { return ctx ? ctx->arena_bytes : 0; }
+
+uint64_t dm_launch_count(const dm_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+dm_status dm_merge_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* stream,
+                          uint32_t flags) {
+  if (!ctx) return DM_EINVAL;
+  dm_status st = check_column(in, out, true);
+  if (st != DM_OK) return st;
+  if (dm_scratch_bytes(in, flags) > ctx->arena_bytes) return DM_ENOMEM;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  const bool timing = (flags & DM_FLAG_TIMING) != 0;
+  if (timing && !ctx->ring) {
+    ctx->ring = new (std::nothrow) cudaEvent_t[4 * dm_ctx::kRing]();
+    if (!ctx->ring) return DM_ENOMEM;
+    for (uint32_t i = 0; i < 4 * dm_ctx::kRing; ++i)
+      if (cudaEventCreate(&ctx->ring[i]) != cudaSuccess) return DM_ECUDA;
+  }
+  cudaEvent_t* ev = nullptr;
+  if (timing) ev = ctx->ring_n < dm_ctx::kRing ? ctx->ring + 4 * ctx->ring_n : ctx->ev;
+  st = run_column(ctx, in, out, ctx->arena, as_stream(stream), flags, ev);
+  ctx->timing_valid = timing && st == DM_OK;
+  if (ctx->timing_valid) {
+    ctx->last_ev = ev;
+    if (ev != ctx->ev) ++ctx->ring_n;
+  }
+  return st;
+}
+
+dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, const dm_column_out* out,
+                         void* stream, uint32_t flags) {
+  if (!ctx || (ncols && (!in || !out))) return DM_EINVAL;
+  for (uint32_t c = 0; c < ncols; ++c) {
+    dm_status st = check_column(&in[c], &out[c], true);
+    if (st != DM_OK) return st;
+  }
+  if (dm_table_scratch_bytes(in, ncols, flags) > ctx->arena_bytes) return DM_ENOMEM;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  // columns are independent tasks; on one stream they reuse one scratch region
+  for (uint32_t c = 0; c < ncols; ++c) {
+    dm_status st = run_column(ctx, &in[c], &out[c], ctx->arena, as_stream(stream), flags, nullptr);
+    if (st != DM_OK) return st;
+  }
+  ctx->timing_valid = false;
+  return DM_OK;
+}
+
+size_t dm_host_scratch_bytes(const dm_column_in* in, uint32_t flags) {
+  if (!in) return 0;
+  const uint32_t w = in->value_bytes;
+  const uint64_t m = in->main_dict_len, d = in->delta_dict_len;
+  const uint64_t n_out = in->main_rows + in->delta_rows;
+  size_t b = 0;
+  b += align_up(m * w) + align_up(dm_packed_bytes(in->main_rows, in->main_bits));
+  b += align_up(d * w) + align_up(in->delta_rows * 4);
+  b += align_up((m + d) * w) + align_up(dm_packed_bytes(n_out, bits_for(m + d)));
+  b += align_up(m * 4) + align_up(d * 4) + align_up(16);
+  return b + dm_scratch_bytes(in, flags);
+}
+
+dm_status dm_merge_column_host(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* stream,
+                               uint32_t flags, uint64_t* new_dict_len, uint32_t* new_bits) {
+  if (!ctx || !new_dict_len || !new_bits) return DM_EINVAL;
+  dm_status st = check_column(in, out, false);
+  if (st != DM_OK) return st;
+  if (dm_host_scratch_bytes(in, flags) > ctx->arena_bytes) return DM_ENOMEM;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  cudaStream_t s = as_stream(stream);
+  const uint32_t w = in->value_bytes;
+  const uint64_t m = in->main_dict_len, d = in->delta_dict_len;
+  const uint64_t n_out = in->main_rows + in->delta_rows;
+  const size_t main_bytes = dm_packed_bytes(in->main_rows, in->main_bits);
+
+  Carver c(ctx->arena);
+  dm_column_in din = *in;
+  dm_column_out dout{};
+  void* p_main_dict = c.take(m * w);
+  void* p_main = c.take(main_bytes);
+  void* p_ddict = c.take(d * w);
+  void* p_dcodes = c.take(in->delta_rows * 4);
+  dout.new_dict = c.take((m + d) * w);
+  dout.new_packed = c.take(dm_packed_bytes(n_out, bits_for(m + d)));
+  dout.x_main = static_cast<uint32_t*>(c.take(m * 4));
+  dout.x_delta = static_cast<uint32_t*>(c.take(d * 4));
+  char* scal = static_cast<char*>(c.take(16));
+  dout.d_new_dict_len = reinterpret_cast<uint64_t*>(scal);
+  dout.d_new_bits = reinterpret_cast<uint32_t*>(scal + 8);
+  void* scratch = c.take(0);
+  din.main_dict = p_main_dict;
+  din.main_packed = p_main;
+  din.delta_dict = p_ddict;
+  din.delta_codes = static_cast<const uint32_t*>(p_dcodes);
+
+  cudaError_t e = cudaSuccess;
+  // dictionaries and delta codes on the merge stream; the large main stream
+  // on the copy stream so that its upload overlaps Steps 1(a) and 1(b)
+  if (m) e = cudaMemcpyAsync(p_main_dict, in->main_dict, m * w, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && d) e = cudaMemcpyAsync(p_ddict, in->delta_dict, d * w, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && in->delta_rows)
+    e = cudaMemcpyAsync(p_dcodes, in->delta_codes, in->delta_rows * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && main_bytes) {
+    e = cudaEventRecord(ctx->copy_done, s);  // copy stream starts after earlier work on s
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_done, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p_main, in->main_packed, main_bytes, cudaMemcpyHostToDevice, ctx->copy_stream);
+  }
+  if (e != cudaSuccess) return DM_ECUDA;
+
+  // Steps 1(a), 1(b)+2(a) on s (overlapping the main upload), then 2(b)
+  dm_column_in stage1 = din;
+  stage1.main_rows = 0;
+  stage1.delta_rows = 0;
+  st = run_column(ctx, &stage1, &dout, scratch, s, flags, nullptr);
+  if (st != DM_OK) return st;
+  if (main_bytes) {
+    if (cudaEventRecord(ctx->copy_done, ctx->copy_stream) != cudaSuccess ||
+        cudaStreamWaitEvent(s, ctx->copy_done, 0) != cudaSuccess)
+      return DM_ECUDA;
+  }
+  if (n_out) {
+    // X tables now live in dout; re-encode only
+    dm::ReencodeArgs ra;
+    ra.main_words = static_cast<const uint32_t*>(din.main_packed);
+    ra.main_words_n = main_bytes / 4;
+    ra.n_main = din.main_rows;
+    ra.dcodes = din.delta_codes;
+    ra.n_delta = din.delta_rows;
+    ra.xm = dout.x_main;
+    ra.m = (uint32_t)m;
+    ra.xd = dout.x_delta;
+    ra.d = (uint32_t)d;
+    ra.d_bits = dout.d_new_bits;
+    ra.max_bits = bits_for(m + d);
+    ra.out_words = static_cast<uint32_t*>(dout.new_packed);
+    ra.status = ctx->status;
+    e = dm::launch_reencode(din.main_bits, ra, s, ctx->sm_count, flags, &ctx->launches);
+    if (e != cudaSuccess) return DM_ECUDA;
+  }
+  uint64_t hs[2] = {0, 0};
+  e = cudaMemcpyAsync(hs, scal, 16, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return DM_ECUDA;
+  const uint64_t u = hs[0];
+  const uint32_t bn = (uint32_t)(hs[1] & 0xFFFFFFFFu);
+  if (u > m + d || bn > 32) return DM_ETIMEOUT;
+  *new_dict_len = u;
+  *new_bits = bn;
+  if (u) e = cudaMemcpyAsync(out->new_dict, dout.new_dict, u * w, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && n_out && bn)
+    e = cudaMemcpyAsync(out->new_packed, dout.new_packed, dm_packed_bytes(n_out, bn), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && out->x_main && m)
+    e = cudaMemcpyAsync(out->x_main, dout.x_main, m * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && out->x_delta && d)
+    e = cudaMemcpyAsync(out->x_delta, dout.x_delta, d * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return cuda_status(e);
+}
+
+dm_status dm_sort_delta(dm_ctx* ctx, uint32_t w, const void* delta_dict, uint64_t d, void* ud_out,
+                        uint32_t* perm_out, void* stream) {
+  if (!ctx || !width_ok(w) || d >= (1ull << 30)) return DM_EINVAL;
+  if (d == 0) return DM_OK;
+  const size_t ka = w;
+  if (!delta_dict || !ud_out || !perm_out || !aligned(delta_dict, ka) || !aligned(ud_out, ka)) return DM_EINVAL;
+  dm_column_in in{};
+  in.value_bytes = w;
+  in.delta_dict = delta_dict;
+  in.delta_dict_len = d;
+  if (dm_scratch_bytes(&in, 0) > ctx->arena_bytes) return DM_ENOMEM;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  cudaStream_t s = as_stream(stream);
+  ColumnScratch cs;
+  carve_column(ctx->arena, &in, nullptr, &cs);
+  if (cudaMemsetAsync(cs.zero, 0, cs.zero_bytes, s) != cudaSuccess) return DM_ECUDA;
+  cs.sort.status = ctx->status;
+  if (dm::launch_sort(w, cs.sort, s, ctx->sm_count, &ctx->launches) != cudaSuccess) return DM_ECUDA;
+  return cuda_status(dm::launch_sort_copy_out(w, cs.slots, d, ud_out, perm_out, s, &ctx->launches));
+}
+
+dm_status dm_merge_dicts(dm_ctx* ctx, uint32_t w, const void* main_dict, uint64_t m, const void* ud,
+                         const uint32_t* perm, uint64_t d, void* new_dict, uint32_t* x_main, uint32_t* x_delta,
+                         uint64_t* d_u, uint32_t* d_bits, void* stream) {
+  if (!ctx || !width_ok(w) || m + d > (1ull << 32) || !d_u || !d_bits) return DM_EINVAL;
+  if ((m && (!main_dict || !x_main)) || (d && (!ud || !perm || !x_delta)) || (m + d && !new_dict)) return DM_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  cudaStream_t s = as_stream(stream);
+  if (m + d == 0) {
+    if (cudaMemsetAsync(d_u, 0, 8, s) != cudaSuccess || cudaMemsetAsync(d_bits, 0, 4, s) != cudaSuccess)
+      return DM_ECUDA;
+    return DM_OK;
+  }
+  const uint32_t mt = dm::merge_tiles(m + d);
+  const size_t need = align_up((size_t)mt * 8 + 8);
+  if (need > ctx->arena_bytes) return DM_ENOMEM;
+  uint64_t* lb = static_cast<uint64_t*>(ctx->arena);
+  if (cudaMemsetAsync(lb, 0, (size_t)mt * 8 + 8, s) != cudaSuccess) return DM_ECUDA;
+  dm::MergeArgs a{};
+  a.a = main_dict;
+  a.m = m;
+  a.b = ud;
+  a.perm = perm;
+  a.b_slot = nullptr;
+  a.d = d;
+  a.unew = new_dict;
+  a.xm = x_main;
+  a.xd = x_delta;
+  a.d_u = d_u;
+  a.d_bits = d_bits;
+  a.lookback = lb;
+  a.counter = reinterpret_cast<uint32_t*>(lb + mt);
+  a.ntiles = mt;
+  a.status = ctx->status;
+  return cuda_status(dm::launch_merge(w, a, s, &ctx->launches));
+}
+
+dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bits, uint64_t n_main,
+                      const uint32_t* delta_codes, uint64_t n_delta, const uint32_t* x_main, uint64_t m,
+                      const uint32_t* x_delta, uint64_t d, const uint32_t* d_bits, uint32_t max_bits,
+                      uint32_t* out_packed, void* stream, uint32_t flags) {
+  if (!ctx || main_bits > 32 || max_bits > 32 || !d_bits || m > 0xFFFFFFFFull || d > 0xFFFFFFFFull)
+    return DM_EINVAL;
+  if ((n_main && (!m || !x_main || (main_bits && (!main_packed || !aligned(main_packed, 16))))) ||
+      (n_delta && (!d || !x_delta || !delta_codes)))
+    return DM_EINVAL;
+  if (n_main + n_delta && max_bits && (!out_packed || !aligned(out_packed, 16))) return DM_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  dm::ReencodeArgs ra;
+  ra.main_words = main_packed;
+  ra.main_words_n = dm_packed_bytes(n_main, main_bits) / 4;
+  ra.n_main = n_main;
+  ra.dcodes = delta_codes;
+  ra.n_delta = n_delta;
+  ra.xm = x_main;
+  ra.m = (uint32_t)m;
+  ra.xd = x_delta;
+  ra.d = (uint32_t)d;
+  ra.d_bits = d_bits;
+  ra.max_bits = max_bits;
+  ra.out_words = out_packed;
+  ra.status = ctx->status;
+  return cuda_status(dm::launch_reencode(main_bits, ra, as_stream(stream), ctx->sm_count, flags, &ctx->launches));
+}
+
+dm_status dm_sync_status(dm_ctx* ctx, void* stream) {
+  if (!ctx) return DM_EINVAL;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemcpyAsync(ctx->host_status, ctx->status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DM_ECUDA;
+  const uint32_t v = *ctx->host_status;
+  if (v) {
+    if (cudaMemsetAsync(ctx->status, 0, 4, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+      return DM_ECUDA;
+  }
+  if (v & dm::ST_TIMEOUT) return DM_ETIMEOUT;
+  if (v & dm::ST_UNSORTED) return DM_EUNSORTED;
+  if (v & dm::ST_CODE) return DM_ECODE;
+  if (v & dm::ST_WIDTH) return DM_EINVAL;
+  return DM_OK;
+}
+
+static dm_status elapsed4(cudaEvent_t* ev, float ms[4]) {
+  if (cudaEventSynchronize(ev[3]) != cudaSuccess) return DM_ECUDA;
+  if (cudaEventElapsedTime(&ms[0], ev[0], ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(&ms[1], ev[1], ev[2]) != cudaSuccess ||
+      cudaEventElapsedTime(&ms[2], ev[2], ev[3]) != cudaSuccess ||
+      cudaEventElapsedTime(&ms[3], ev[0], ev[3]) != cudaSuccess)
+    return DM_ECUDA;
+  return DM_OK;
+}
+
+dm_status dm_last_timing(dm_ctx* ctx, float ms[4]) {
+  if (!ctx || !ms || !ctx->timing_valid || !ctx->last_ev) return DM_EINVAL;
+  return elapsed4(ctx->last_ev, ms);
+}
+
+dm_status dm_timing_sum(dm_ctx* ctx, float ms[4], uint32_t* calls) {
+  if (!ctx || !ms || !calls) return DM_EINVAL;
+  for (int k = 0; k < 4; ++k) ms[k] = 0.f;
+  *calls = 0;
+  for (uint32_t i = 0; i < ctx->ring_n; ++i) {
+    float one[4];
+    dm_status st = elapsed4(ctx->ring + 4 * i, one);
+    if (st != DM_OK) return st;
+    for (int k = 0; k < 4; ++k) ms[k] += one[k];
+  }
+  *calls = ctx->ring_n;
+  ctx->ring_n = 0;
+  ctx->timing_valid = false;
+  ctx->last_ev = nullptr;
+  return DM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,383 @@
+"""Python binding of libdmerge (include/dmerge.h): argument marshalling only.
+
+The functions below carry the C ABI's names and forward to it through
+ctypes; every step of the merge runs in the library's CUDA kernels.  Device
+memory and streams come from PyTorch: pass tensors (their data pointers are
+taken) and a torch.cuda.Stream (or None for the current stream).
+
+There is no fallback: if libdmerge.so is missing or cannot be loaded,
+``load()`` raises.  Build it with ``paper_1109_6885_gb300.build.build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_lock = threading.Lock()
+
+DM_OK, DM_EINVAL, DM_ENOMEM, DM_EUNSORTED, DM_ECODE, DM_ECUDA, DM_ETIMEOUT, DM_EBUSY = range(8)
+DM_FLAG_GENERIC_REENCODE = 0x1
+DM_FLAG_X_SMEM = 0x2
+DM_FLAG_X_GLOBAL = 0x4
+DM_FLAG_TIMING = 0x8
+
+EXPORTS = [
+    "dm_create", "dm_destroy", "dm_reserve", "dm_arena_bytes", "dm_packed_bytes", "dm_bits_for",
+    "dm_max_bits", "dm_scratch_bytes", "dm_merge_column", "dm_merge_table",
+    "dm_table_scratch_bytes", "dm_merge_column_host", "dm_host_scratch_bytes", "dm_sort_delta",
+    "dm_merge_dicts", "dm_reencode", "dm_sync_status", "dm_last_timing", "dm_timing_sum",
+    "dm_launch_count",
+    "dm_status_str",
+]
+
+
+class DmError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        name = _load().dm_status_str(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {name}")
+
+
+class ColumnIn(ctypes.Structure):
+    _fields_ = [
+        ("value_bytes", ctypes.c_uint32),
+        ("main_dict", ctypes.c_void_p),
+        ("main_dict_len", ctypes.c_uint64),
+        ("main_packed", ctypes.c_void_p),
+        ("main_bits", ctypes.c_uint32),
+        ("main_rows", ctypes.c_uint64),
+        ("delta_dict", ctypes.c_void_p),
+        ("delta_dict_len", ctypes.c_uint64),
+        ("delta_codes", ctypes.c_void_p),
+        ("delta_rows", ctypes.c_uint64),
+    ]
+
+
+class ColumnOut(ctypes.Structure):
+    _fields_ = [
+        ("new_dict", ctypes.c_void_p),
+        ("new_packed", ctypes.c_void_p),
+        ("x_main", ctypes.c_void_p),
+        ("x_delta", ctypes.c_void_p),
+        ("d_new_dict_len", ctypes.c_void_p),
+        ("d_new_bits", ctypes.c_void_p),
+    ]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libdmerge.so (raises when it is absent)."""
+    return _load()
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libdmerge.so not built ({path}); run "
+                               "paper_1109_6885_gb300.build.build() — there is no CPU fallback")
+        lib = ctypes.CDLL(path)
+        vp, u32, u64, sz, i32 = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t,
+                                 ctypes.c_int)
+        pin, pout = ctypes.POINTER(ColumnIn), ctypes.POINTER(ColumnOut)
+        sig = {
+            "dm_create": ([ctypes.POINTER(vp), i32, sz], i32),
+            "dm_destroy": ([vp], None),
+            "dm_reserve": ([vp, sz], i32),
+            "dm_arena_bytes": ([vp], sz),
+            "dm_packed_bytes": ([u64, u32], sz),
+            "dm_bits_for": ([u64], u32),
+            "dm_max_bits": ([pin], u32),
+            "dm_scratch_bytes": ([pin, u32], sz),
+            "dm_merge_column": ([vp, pin, pout, vp, u32], i32),
+            "dm_merge_table": ([vp, pin, u32, pout, vp, u32], i32),
+            "dm_table_scratch_bytes": ([pin, u32, u32], sz),
+            "dm_merge_column_host": ([vp, pin, pout, vp, u32, ctypes.POINTER(u64),
+                                      ctypes.POINTER(u32)], i32),
+            "dm_host_scratch_bytes": ([pin, u32], sz),
+            "dm_sort_delta": ([vp, u32, vp, u64, vp, vp, vp], i32),
+            "dm_merge_dicts": ([vp, u32, vp, u64, vp, vp, u64, vp, vp, vp, vp, vp, vp], i32),
+            "dm_reencode": ([vp, vp, u32, u64, vp, u64, vp, u64, vp, u64, vp, u32, vp, vp, u32],
+                            i32),
+            "dm_sync_status": ([vp, vp], i32),
+            "dm_last_timing": ([vp, ctypes.POINTER(ctypes.c_float)], i32),
+            "dm_timing_sum": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(u32)], i32),
+            "dm_launch_count": ([vp], u64),
+            "dm_status_str": ([i32], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, what: str):
+    if rc != DM_OK:
+        raise DmError(rc, what)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data if t.size else None
+    return t.data_ptr() if t.numel() else None
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream or None
+    if isinstance(stream, int):
+        return stream or None
+    return stream.cuda_stream or None
+
+
+# ------------------------------------------------------------------ thin wrappers
+
+def dm_packed_bytes(rows: int, bits: int) -> int:
+    return int(_load().dm_packed_bytes(rows, bits))
+
+
+def dm_bits_for(n: int) -> int:
+    return int(_load().dm_bits_for(n))
+
+
+def dm_max_bits(cin: ColumnIn) -> int:
+    return int(_load().dm_max_bits(ctypes.byref(cin)))
+
+
+def dm_scratch_bytes(cin: ColumnIn, flags: int = 0) -> int:
+    return int(_load().dm_scratch_bytes(ctypes.byref(cin), flags))
+
+
+def dm_host_scratch_bytes(cin: ColumnIn, flags: int = 0) -> int:
+    return int(_load().dm_host_scratch_bytes(ctypes.byref(cin), flags))
+
+
+def dm_table_scratch_bytes(cins, flags: int = 0) -> int:
+    arr = (ColumnIn * len(cins))(*cins)
+    return int(_load().dm_table_scratch_bytes(arr, len(cins), flags))
+
+
+class Context:
+    """Owns a dm_ctx (device, scratch arena, status word)."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 0):
+        self.handle = ctypes.c_void_p()
+        _check(_load().dm_create(ctypes.byref(self.handle), device, arena_bytes), "dm_create")
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            _load().dm_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, nbytes: int):
+        _check(_load().dm_reserve(self.handle, nbytes), "dm_reserve")
+
+    @property
+    def arena_bytes(self) -> int:
+        return int(_load().dm_arena_bytes(self.handle))
+
+    @property
+    def launches(self) -> int:
+        return int(_load().dm_launch_count(self.handle))
+
+    def sync_status(self, stream=None) -> int:
+        return int(_load().dm_sync_status(self.handle, _stream(stream)))
+
+    def last_timing(self):
+        """ms of Step 1(a), 1(b)+2(a), 2(b) and the whole last timed merge."""
+        ms = (ctypes.c_float * 4)()
+        _check(_load().dm_last_timing(self.handle, ms), "dm_last_timing")
+        return list(ms)
+
+    def timing_sum(self):
+        """(summed ms per step as in last_timing, number of timed calls); resets."""
+        ms = (ctypes.c_float * 4)()
+        n = ctypes.c_uint32(0)
+        _check(_load().dm_timing_sum(self.handle, ms, ctypes.byref(n)), "dm_timing_sum")
+        return list(ms), int(n.value)
+
+
+def dm_merge_column(ctx: Context, cin: ColumnIn, cout: ColumnOut, stream=None, flags: int = 0):
+    _check(_load().dm_merge_column(ctx.handle, ctypes.byref(cin), ctypes.byref(cout),
+                                   _stream(stream), flags), "dm_merge_column")
+
+
+def dm_merge_table(ctx: Context, cins, couts, stream=None, flags: int = 0):
+    n = len(cins)
+    ain = (ColumnIn * n)(*cins)
+    aout = (ColumnOut * n)(*couts)
+    _check(_load().dm_merge_table(ctx.handle, ain, n, aout, _stream(stream), flags),
+           "dm_merge_table")
+
+
+def dm_merge_column_host(ctx: Context, cin: ColumnIn, cout: ColumnOut, stream=None,
+                         flags: int = 0):
+    u = ctypes.c_uint64(0)
+    b = ctypes.c_uint32(0)
+    _check(_load().dm_merge_column_host(ctx.handle, ctypes.byref(cin), ctypes.byref(cout),
+                                        _stream(stream), flags, ctypes.byref(u), ctypes.byref(b)),
+           "dm_merge_column_host")
+    return int(u.value), int(b.value)
+
+
+def dm_sort_delta(ctx: Context, w: int, delta_dict, d: int, ud_out, perm_out, stream=None):
+    _check(_load().dm_sort_delta(ctx.handle, w, _ptr(delta_dict), d, _ptr(ud_out), _ptr(perm_out),
+                                 _stream(stream)), "dm_sort_delta")
+
+
+def dm_merge_dicts(ctx: Context, w: int, main_dict, m: int, ud, perm, d: int, new_dict, x_main,
+                   x_delta, d_u, d_bits, stream=None):
+    _check(_load().dm_merge_dicts(ctx.handle, w, _ptr(main_dict), m, _ptr(ud), _ptr(perm), d,
+                                  _ptr(new_dict), _ptr(x_main), _ptr(x_delta), _ptr(d_u),
+                                  _ptr(d_bits), _stream(stream)), "dm_merge_dicts")
+
+
+def dm_reencode(ctx: Context, main_packed, main_bits: int, n_main: int, delta_codes, n_delta: int,
+                x_main, m: int, x_delta, d: int, d_bits, max_bits: int, out_packed, stream=None,
+                flags: int = 0):
+    _check(_load().dm_reencode(ctx.handle, _ptr(main_packed), main_bits, n_main, _ptr(delta_codes),
+                               n_delta, _ptr(x_main), m, _ptr(x_delta), d, _ptr(d_bits), max_bits,
+                               _ptr(out_packed), _stream(stream), flags), "dm_reencode")
+
+
+# ------------------------------------------------------------------ tensor helpers
+
+_SIGNED = {np.dtype(np.uint32): np.int32, np.dtype(np.uint64): np.int64}
+
+
+def to_device(a: np.ndarray, device="cuda"):
+    """numpy (unsigned) array -> torch tensor on the device (same bytes)."""
+    import torch
+    a = np.ascontiguousarray(a)
+    sa = a.view(_SIGNED.get(a.dtype, a.dtype))
+    if sa.size == 0:
+        return torch.empty(sa.shape, dtype=torch.from_numpy(sa[:0].copy()).dtype, device=device)
+    return torch.from_numpy(sa).to(device)
+
+
+def to_host(t, dtype) -> np.ndarray:
+    """torch tensor -> numpy array reinterpreted as `dtype` (unsigned)."""
+    return t.detach().cpu().numpy().view(dtype)
+
+
+def key_tensor_empty(n: int, w: int, device="cuda"):
+    import torch
+    if w == 4:
+        return torch.empty(n, dtype=torch.int32, device=device)
+    if w == 8:
+        return torch.empty(n, dtype=torch.int64, device=device)
+    return torch.empty((n, 2), dtype=torch.int64, device=device)
+
+
+def key_np_dtype(w: int):
+    return np.uint32 if w == 4 else np.uint64
+
+
+@dataclasses.dataclass
+class DeviceColumn:
+    """A column's inputs resident in device memory (torch tensors)."""
+    w: int
+    main_dict: object
+    m: int
+    main_packed: object
+    main_bits: int
+    n_main: int
+    delta_dict: object
+    d: int
+    delta_codes: object
+    n_delta: int
+
+    def cin(self) -> ColumnIn:
+        return ColumnIn(self.w, _ptr(self.main_dict), self.m, _ptr(self.main_packed),
+                        self.main_bits, self.n_main, _ptr(self.delta_dict), self.d,
+                        _ptr(self.delta_codes), self.n_delta)
+
+    @staticmethod
+    def from_numpy(w, main_dict, main_packed, main_bits, n_main, delta_dict, delta_codes,
+                   device="cuda"):
+        return DeviceColumn(w, to_device(main_dict, device), int(main_dict.shape[0]),
+                            to_device(main_packed, device), int(main_bits), int(n_main),
+                            to_device(delta_dict, device), int(delta_dict.shape[0]),
+                            to_device(delta_codes, device), int(delta_codes.size))
+
+
+@dataclasses.dataclass
+class DeviceResult:
+    """Output buffers of one column merge (torch tensors, device)."""
+    new_dict: object
+    new_packed: object
+    x_main: object
+    x_delta: object
+    scalars: object       # int64[2]: |U'| then E'_C (low 32 bits)
+
+    def cout(self) -> ColumnOut:
+        base = self.scalars.data_ptr()
+        return ColumnOut(_ptr(self.new_dict), _ptr(self.new_packed), _ptr(self.x_main),
+                         _ptr(self.x_delta), base, base + 8)
+
+    def u_bits(self):
+        s = self.scalars.cpu().numpy()
+        return int(s[0]), int(s[1] & 0xFFFFFFFF)
+
+
+def alloc_result(col: DeviceColumn, device="cuda", with_x: bool = True) -> DeviceResult:
+    import torch
+    maxb = dm_bits_for(col.m + col.d)
+    nbytes = dm_packed_bytes(col.n_main + col.n_delta, maxb)
+    return DeviceResult(
+        key_tensor_empty(col.m + col.d, col.w, device),
+        torch.empty(max(nbytes // 4, 0), dtype=torch.int32, device=device),
+        torch.empty(col.m, dtype=torch.int32, device=device) if with_x else None,
+        torch.empty(col.d, dtype=torch.int32, device=device) if with_x else None,
+        torch.zeros(2, dtype=torch.int64, device=device),
+    )
+
+
+def merge_column(ctx: Context, col: DeviceColumn, res: DeviceResult | None = None, stream=None,
+                 flags: int = 0) -> DeviceResult:
+    """dm_merge_column on a DeviceColumn; grows the arena when needed."""
+    cin = col.cin()
+    need = dm_scratch_bytes(cin, flags)
+    if need > ctx.arena_bytes:
+        ctx.reserve(need)
+    if res is None:
+        res = alloc_result(col)
+    dm_merge_column(ctx, cin, res.cout(), stream, flags)
+    return res
+
+
+def fetch(res: DeviceResult, w: int, n_out: int):
+    """Copy a merge result back: (U', X_M, X_D, packed words, E'_C, |U'|)."""
+    u, b = res.u_bits()
+    kd = key_np_dtype(w)
+    new_dict = to_host(res.new_dict[:u], kd)
+    nwords = dm_packed_bytes(n_out, b) // 4
+    packed = to_host(res.new_packed[:nwords], np.uint32)
+    xm = to_host(res.x_main, np.uint32) if res.x_main is not None else None
+    xd = to_host(res.x_delta, np.uint32) if res.x_delta is not None else None
+    return new_dict, xm, xd, packed, b, u

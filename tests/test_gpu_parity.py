@@ -1,0 +1,352 @@
+"""CUDA path vs the CPU oracle, element by element (exact: all integer work).
+
+Covers each step through its own C-ABI entry point, the whole column merge
+on the workload shapes (sizes the oracle finishes in seconds, spanning many
+tiles with ragged tails), the edge cases of the method, the error paths
+(recorded in the status word, never faulting), determinism, and the
+host-buffer and table entry points.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1109_6885_gb300 import dmerge as dm
+from tests import _brute
+from tests.gpu_util import assert_parity, column_from_lists, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1109_6885_gb300 import build
+    build.build()
+    c = dm.Context(0, 64 << 20)
+    yield c
+    c.close()
+
+
+def kd(w):
+    return dm.key_np_dtype(w)
+
+
+# ------------------------------------------------------------------ Step 1(a)
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+@pytest.mark.parametrize("d", [1, 2, 31, 2047, 2048, 2049, 40_000, 300_001])
+def test_sort_delta_parity(ctx, w, d):
+    import torch
+    keys = synth.dictionary(synth.subseed(d, w), w, d)
+    rng = np.random.default_rng(d + w)
+    order = rng.permutation(d)
+    dd = keys[order]
+    if d > 10:   # duplicates inside D_dict
+        dd[rng.integers(0, d, d // 10)] = dd[rng.integers(0, d, d // 10)]
+    ud_ref, perm_ref = oracle.sort_delta(w, dd)
+    t_in = dm.to_device(dd)
+    ud = dm.key_tensor_empty(d, w)
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    dm.dm_sort_delta(ctx, w, t_in, d, ud, perm)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_OK
+    assert np.array_equal(dm.to_host(ud, kd(w)), ud_ref)
+    assert np.array_equal(dm.to_host(perm, np.uint32), perm_ref)
+
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+def test_sort_constant_digits(ctx, w):
+    """Keys sharing most bytes (skipped passes), all-equal keys, equal hi words."""
+    import torch
+    rng = np.random.default_rng(7)
+    d = 9000
+    if w == 16:
+        dd = np.zeros((d, 2), np.uint64)
+        dd[:, 0] = 0xABCDEF
+        dd[:, 1] = rng.integers(0, 300, d).astype(np.uint64)
+    else:
+        dd = (rng.integers(0, 200, d).astype(kd(w)) << kd(w)(8)) | kd(w)(0x11)
+    for arr in (dd, dd[:1].repeat(d, axis=0)):
+        ud_ref, perm_ref = oracle.sort_delta(w, arr)
+        ud = dm.key_tensor_empty(d, w)
+        perm = torch.empty(d, dtype=torch.int32, device="cuda")
+        dm.dm_sort_delta(ctx, w, dm.to_device(arr), d, ud, perm)
+        torch.cuda.synchronize()
+        assert np.array_equal(dm.to_host(ud, kd(w)), ud_ref)
+        assert np.array_equal(dm.to_host(perm, np.uint32), perm_ref)
+
+
+# ------------------------------------------------------------------ Step 1(b) + 2(a)
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+@pytest.mark.parametrize("m,d", [(0, 5), (5, 0), (1, 1), (2048, 1), (3000, 5000), (100_000, 9_000),
+                                 (7, 70_000), (250_000, 250_000)])
+def test_merge_dicts_parity(ctx, w, m, d):
+    import torch
+    um = synth.dictionary(synth.subseed(m, 1), w, m)
+    rng = np.random.default_rng(m * 7 + d)
+    fresh = synth.dictionary(synth.subseed(d, 2), w, d)
+    dd = fresh.copy()
+    if m and d:   # about a third of the delta values are main values
+        k = d // 3
+        dd[:k] = um[rng.integers(0, m, k)]
+        dd = dd[rng.permutation(d)]
+    ud_ref, perm_ref = oracle.sort_delta(w, dd)
+    new_ref, xm_ref, xd_ref = oracle.merge_dicts(w, um, ud_ref, perm_ref)
+    new = dm.key_tensor_empty(m + d, w)
+    xm = torch.empty(m, dtype=torch.int32, device="cuda")
+    xd = torch.empty(d, dtype=torch.int32, device="cuda")
+    sc = torch.zeros(2, dtype=torch.int64, device="cuda")
+    dm.dm_merge_dicts(ctx, w, dm.to_device(um), m, dm.to_device(ud_ref), dm.to_device(perm_ref), d,
+                      new, xm, xd, sc, sc[1:], None)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_OK
+    u, b = int(sc[0]), int(sc[1]) & 0xFFFFFFFF
+    assert u == new_ref.shape[0]
+    assert b == oracle.new_width(u)
+    assert np.array_equal(dm.to_host(new[:u], kd(w)), new_ref)
+    assert np.array_equal(dm.to_host(xm, np.uint32), xm_ref)
+    assert np.array_equal(dm.to_host(xd, np.uint32), xd_ref)
+
+
+# ------------------------------------------------------------------ Step 2(b)
+
+@pytest.mark.parametrize("b", list(range(0, 33)))
+def test_reencode_every_width(ctx, b):
+    """Every input width, output widths b-1, b, b+1 and a distant one; ragged tails."""
+    import torch
+    rng = np.random.default_rng(b)
+    m = min(2**b, 5000) if b else 1
+    n_main, n_delta, d = 70_003, 1_234, 77
+    mc = rng.integers(0, m, n_main).astype(np.uint32)
+    dc = rng.integers(0, d, n_delta).astype(np.uint32)
+    main = synth.pack(mc, b)
+    for bo in sorted({max(b - 1, 0), b, min(b + 1, 32), (b + 13) % 33}):
+        top = 2**bo
+        xm = rng.integers(0, top, m, dtype=np.uint64).astype(np.uint32)
+        xd = rng.integers(0, top, d, dtype=np.uint64).astype(np.uint32)
+        want = oracle.reencode(main, b, n_main, dc, xm, xd, bo)
+        maxb = max(bo, 20)
+        out = torch.full((dm.dm_packed_bytes(n_main + n_delta, maxb) // 4,), -1, dtype=torch.int32,
+                         device="cuda")
+        bits = torch.tensor([bo], dtype=torch.int32, device="cuda")
+        for flags in (0, dm.DM_FLAG_GENERIC_REENCODE, dm.DM_FLAG_X_SMEM, dm.DM_FLAG_X_GLOBAL):
+            out.fill_(-1)
+            dm.dm_reencode(ctx, dm.to_device(main), b, n_main, dm.to_device(dc), n_delta,
+                           dm.to_device(xm), m, dm.to_device(xd), d, bits, maxb, out, None, flags)
+            torch.cuda.synchronize()
+            assert ctx.sync_status() == dm.DM_OK
+            got = dm.to_host(out, np.uint32)
+            assert np.array_equal(got[:want.size], want), (b, bo, flags)
+            assert np.all(got[want.size:] == 0xFFFFFFFF), "wrote past the stream's end"
+
+
+# ------------------------------------------------------------------ whole column
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+@pytest.mark.parametrize("dist", ["uniform", "zipf"])
+@pytest.mark.parametrize("n_main,m,n_delta,f_new", [
+    (1, 1, 1, 0.5), (31, 5, 33, 0.5), (1023, 40, 1, 1.0), (1025, 1000, 1023, 0.3),
+    (33_333, 2_000, 3_333, 0.3), (250_007, 100_000, 20_011, 0.5), (100_000, 60_000, 100_000, 0.9),
+])
+def test_merge_column_parity(ctx, w, dist, n_main, m, n_delta, f_new):
+    spec = synth.ColumnSpec(n_main=n_main, m=m, w=w, n_delta=n_delta, f_new=f_new, dist=dist,
+                            zipf_s=0.8, seed=n_main ^ (m << 8) ^ w)
+    assert_parity(ctx, synth.make_column(spec))
+
+
+def test_small_single_column_workload(ctx):
+    """1,000,000 rows over 100,000 uint64 values at 17 bits; 10,000 delta rows, half new."""
+    spec = synth.ColumnSpec(n_main=1_000_000, m=100_000, w=8, n_delta=10_000, f_new=0.5, pool=0,
+                            seed=synth.column_seed(1, 0))
+    col = synth.make_column(spec)
+    ref = assert_parity(ctx, col)
+    assert col.main_bits == 17 and ref.new_bits == 17
+    for flags in (dm.DM_FLAG_X_SMEM, dm.DM_FLAG_X_GLOBAL, dm.DM_FLAG_GENERIC_REENCODE):
+        assert_parity(ctx, col, flags, ref)
+
+
+@pytest.mark.parametrize("case", ["delta_empty", "main_empty", "subset_same_width", "all_new",
+                                  "u_one", "u_two", "grow_to_pow2", "cross_pow2", "non_minimal_b",
+                                  "shrink_width"])
+def test_edge_cases(ctx, case):
+    rng = np.random.default_rng(len(case))
+    if case == "delta_empty":
+        col = synth.make_column(synth.ColumnSpec(n_main=5000, m=700, n_delta=0))
+    elif case == "main_empty":
+        col = synth.make_column(synth.ColumnSpec(n_main=0, m=0, n_delta=5000, f_new=1.0))
+    elif case == "subset_same_width":
+        col = synth.make_column(synth.ColumnSpec(n_main=50_000, m=1000, n_delta=3000, f_new=0.0))
+        ref = assert_parity(ctx, col)
+        assert ref.new_bits == col.main_bits
+        nb = col.n_main * col.main_bits // 32
+        assert np.array_equal(ref.new_packed[:nb], col.main_packed[:nb])
+        return
+    elif case == "all_new":
+        col = synth.make_column(synth.ColumnSpec(n_main=20_000, m=500, n_delta=9000, f_new=1.0,
+                                                 pool=0))
+    elif case == "u_one":
+        col = column_from_lists(8, [42], [0] * 3000, [42], [0] * 77)
+    elif case == "u_two":
+        col = column_from_lists(8, [42], [0] * 3000, [43], [0] * 77)
+    elif case == "grow_to_pow2":      # 1000 + 24 new -> 1024: still 10 bits
+        um = sorted(rng.choice(10**6, 1000, replace=False).tolist())
+        new = sorted(set(range(10**6, 10**6 + 24)))
+        col = column_from_lists(4, um, rng.integers(0, 1000, 9999).tolist(), new,
+                                rng.integers(0, 24, 555).tolist())
+    elif case == "cross_pow2":        # 1024 + 1 -> 1025: 10 -> 11 bits
+        um = list(range(0, 2048, 2))
+        col = column_from_lists(4, um, rng.integers(0, 1024, 9999).tolist(), [7],
+                                [0] * 555)
+    elif case == "non_minimal_b":     # main stored wider than needed
+        um = list(range(100, 400))
+        col = column_from_lists(8, um, rng.integers(0, 300, 20_000).tolist(), [5, 999],
+                                [0, 1] * 100, b=23)
+    else:                             # shrink: b' < b
+        um = list(range(100, 116))
+        col = column_from_lists(8, um, rng.integers(0, 16, 20_000).tolist(), [1],
+                                [0] * 100, b=31)
+    assert_parity(ctx, col)
+
+
+def test_extreme_keys_and_equal_hi(ctx):
+    top = 2**64 - 1
+    rng = np.random.default_rng(3)
+    col = column_from_lists(8, [0, 5, top], rng.integers(0, 3, 5000).tolist(), [top, 1, 0, 7],
+                            rng.integers(0, 4, 999).tolist())
+    assert_parity(ctx, col)
+    hi = 0xFEED << 64
+    um = [hi | v for v in range(0, 4000, 3)]
+    dd = [hi | v for v in range(1, 4000, 5)] + [(1 << 64) | 3, 2**128 - 1]
+    col = column_from_lists(16, um, rng.integers(0, len(um), 30_000).tolist(), dd,
+                            rng.integers(0, len(dd), 4000).tolist())
+    assert_parity(ctx, col)
+    # 4-byte keys at collision density: 2^20 main values over a 2^21 range
+    um = sorted(rng.choice(2**21, 2**20, replace=False).tolist())
+    dd = rng.choice(2**21, 50_000, replace=False).tolist()
+    col = column_from_lists(4, um, rng.integers(0, len(um), 300_000).tolist(), dd,
+                            rng.integers(0, len(dd), 60_000).tolist())
+    assert_parity(ctx, col)
+
+
+def test_duplicates_in_delta_dict(ctx):
+    rng = np.random.default_rng(9)
+    um = list(range(0, 30_000, 3))
+    dd = rng.integers(0, 40_000, 5000).tolist()           # repeats inside D_dict
+    col = column_from_lists(8, um, rng.integers(0, len(um), 40_000).tolist(), dd,
+                            rng.integers(0, len(dd), 7000).tolist())
+    assert_parity(ctx, col)
+
+
+def test_determinism(ctx):
+    col = synth.make_column(synth.ColumnSpec(n_main=300_000, m=50_000, n_delta=30_000, f_new=0.3,
+                                             dist="zipf", seed=11))
+    a, _ = run_gpu(ctx, col)
+    b, _ = run_gpu(ctx, col)
+    for x, y in zip(a, b):
+        if isinstance(x, np.ndarray):
+            assert np.array_equal(x, y)
+        else:
+            assert x == y
+
+
+# ------------------------------------------------------------------ errors (no faults)
+
+def test_unsorted_main_dict_is_reported(ctx):
+    col = column_from_lists(8, [5, 3, 9], [0, 1, 2] * 100, [4], [0] * 10)
+    _, st = run_gpu(ctx, col)
+    assert st == dm.DM_EUNSORTED
+    assert ctx.sync_status() == dm.DM_OK          # read-and-clear
+
+
+def test_out_of_range_codes_are_clamped_and_reported(ctx):
+    um = list(range(10, 20))                      # m = 10 at 4 bits: codes 10..15 are invalid
+    codes = [3, 15, 7, 12] * 3000
+    col = column_from_lists(8, um, codes, [1], [0] * 5, b=4)
+    _, st = run_gpu(ctx, col)
+    assert st == dm.DM_ECODE
+    col = column_from_lists(8, um, [1] * 5000, [1, 2], [0, 1, 5])   # delta code 5 >= d = 2
+    _, st = run_gpu(ctx, col)
+    assert st == dm.DM_ECODE
+
+
+def test_argument_errors(ctx):
+    col = synth.make_column(synth.ColumnSpec(n_main=1000, m=100, n_delta=10))
+    dcol = dm.DeviceColumn.from_numpy(col.w, col.main_dict, col.main_packed, col.main_bits,
+                                      col.n_main, col.delta_dict, col.delta_codes)
+    res = dm.alloc_result(dcol)
+    bad = dcol.cin()
+    bad.value_bytes = 6
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_merge_column(ctx, bad, res.cout())
+    assert e.value.status == dm.DM_EINVAL
+    bad = dcol.cin()
+    bad.main_bits = 3                               # below ceil(log2 100)
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_merge_column(ctx, bad, res.cout())
+    assert e.value.status == dm.DM_EINVAL
+    small = dm.Context(0, 1024)
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_merge_column(small, dcol.cin(), res.cout())
+    assert e.value.status == dm.DM_ENOMEM
+    small.close()
+
+
+# ------------------------------------------------------------------ other entry points
+
+def test_host_buffer_entry_point(ctx):
+    col = synth.make_column(synth.ColumnSpec(n_main=400_003, m=30_000, w=16, n_delta=20_000,
+                                             f_new=0.4, dist="zipf", seed=21))
+    ref = oracle.merge_synth_column(col)
+    cin = dm.ColumnIn(col.w, col.main_dict.ctypes.data, col.main_dict.shape[0],
+                      col.main_packed.ctypes.data, col.main_bits, col.n_main,
+                      col.delta_dict.ctypes.data, col.delta_dict.shape[0],
+                      col.delta_codes.ctypes.data, col.n_delta)
+    m, d = col.main_dict.shape[0], col.delta_dict.shape[0]
+    new_dict = synth.key_array(m + d, 16)
+    packed = np.zeros(dm.dm_packed_bytes(col.n_main + col.n_delta, dm.dm_bits_for(m + d)) // 4,
+                      np.uint32)
+    xm = np.zeros(m, np.uint32)
+    xd = np.zeros(d, np.uint32)
+    cout = dm.ColumnOut(new_dict.ctypes.data, packed.ctypes.data, xm.ctypes.data, xd.ctypes.data,
+                        None, None)
+    ctx.reserve(dm.dm_host_scratch_bytes(cin))
+    u, b = dm.dm_merge_column_host(ctx, cin, cout)
+    assert ctx.sync_status() == dm.DM_OK
+    assert u == ref.u and b == ref.new_bits
+    assert np.array_equal(new_dict[:u], ref.new_dict)
+    assert np.array_equal(packed[:ref.new_packed.size], ref.new_packed)
+    assert np.array_equal(xm, ref.x_main) and np.array_equal(xd, ref.x_delta)
+
+
+def test_merge_table_parity(ctx):
+    import torch
+    rng = np.random.default_rng(5)
+    cols, dcols, results = [], [], []
+    n_main, n_delta = 200_000, 3_000
+    for j in range(6):
+        m = int(np.exp(rng.uniform(np.log(2), np.log(150_000))))
+        w = int(rng.choice([4, 8, 16]))
+        spec = synth.ColumnSpec(n_main=n_main, m=m, w=w, n_delta=n_delta,
+                                f_new=float(rng.uniform(0, 0.5)), dist="zipf", zipf_s=0.8,
+                                seed=synth.column_seed(4, j))
+        col = synth.make_column(spec)
+        cols.append(col)
+        dc = dm.DeviceColumn.from_numpy(col.w, col.main_dict, col.main_packed, col.main_bits,
+                                        col.n_main, col.delta_dict, col.delta_codes)
+        dcols.append(dc)
+        results.append(dm.alloc_result(dc))
+    cins = [c.cin() for c in dcols]
+    ctx.reserve(dm.dm_table_scratch_bytes(cins))
+    dm.dm_merge_table(ctx, cins, [r.cout() for r in results])
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_OK
+    for col, res in zip(cols, results):
+        ref = oracle.merge_synth_column(col)
+        new_dict, xm, xd, packed, b, u = dm.fetch(res, col.w, col.n_main + col.n_delta)
+        assert u == ref.u and b == ref.new_bits
+        assert np.array_equal(new_dict, ref.new_dict)
+        assert np.array_equal(packed, ref.new_packed)
+        assert np.array_equal(xm, ref.x_main) and np.array_equal(xd, ref.x_delta)
