@@ -176,6 +176,39 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
                       const uint32_t* d_bits, uint32_t max_bits, uint32_t* out_packed,
                       void* stream, uint32_t flags);
 
+/* ---- allocation-free variant ---- */
+
+/* Largest |U_M| + |U_D| that dm_merge_dicts_noalloc accepts. */
+#define DM_NOALLOC_MAX_ENTRIES (1u << 24)
+
+/* Step 1(b) + 2(a) exactly as dm_merge_dicts, but without a context and
+ * without allocating anything.  The paper has no counterpart: it exists for
+ * callers that must not allocate device memory at merge time — an engine
+ * that has already handed all of HBM to its own fixed pools, or a latency
+ * path where cudaMalloc's implicit device-wide synchronisation (or its
+ * failure when memory is fully reserved) is not acceptable.
+ *
+ * Its scratch (one look-back word per 2048-entry tile plus a tile counter,
+ * at most 64 KiB) is a fixed array in the library's static device memory,
+ * so every GPU that loads libdmerge holds those 64 KiB until the process
+ * exits.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call zeroes the part it uses on
+ * `stream` before its kernel, and the array keeps the last call's contents
+ * afterwards.  All calls on a device share the one array: calls whose work
+ * may overlap on the GPU (different streams without ordering) race, so
+ * serialise them.
+ *
+ * Arguments as dm_merge_dicts; m + d above DM_NOALLOC_MAX_ENTRIES returns
+ * DM_EINVAL.  d_status, if not NULL, is a device word into which the kernel
+ * ORs data errors (1: U_M not strictly increasing, 2: a bad insertion code,
+ * 4: a wait timed out); the caller clears it.  Runs on the current device. */
+dm_status dm_merge_dicts_noalloc(uint32_t value_bytes, const void* main_dict, uint64_t m,
+                                 const void* ud, const uint32_t* perm, uint64_t d,
+                                 void* new_dict, uint32_t* x_main, uint32_t* x_delta,
+                                 uint64_t* d_u, uint32_t* d_bits, uint32_t* d_status,
+                                 void* stream);
+
 /* ---- status, timing, introspection ---- */
 
 /* Wait for `stream`, read and clear the context's device status word:

@@ -18,6 +18,8 @@
 //     from a block scan plus a decoupled look-back over earlier tiles;
 //   * U'[code] receives each non-duplicate, X_M / X_D every position.
 // The last tile publishes |U'| and E'_C = ceil(log2 |U'|) as device scalars.
+#include <mutex>
+
 #include "dm_common.cuh"
 #include "dm_internal.h"
 
@@ -252,3 +254,69 @@ cudaError_t launch_merge(uint32_t w, const MergeArgs& a, cudaStream_t s, uint64_
 }
 
 }  // namespace dm
+
+// ---------------------------------------------------------------- no-alloc variant
+// Scratch of dm_merge_dicts_noalloc: the look-back words of every tile of a
+// merge of up to DM_NOALLOC_MAX_ENTRIES entries, then the tile counter.  It
+// is static device memory of this library, present on every device that
+// loads it; host code must not pass the symbol itself to a kernel (on the
+// host it only names a shadow), so the device address is looked up once per
+// device with cudaGetSymbolAddress.
+namespace {
+constexpr uint32_t kNoAllocTiles = (DM_NOALLOC_MAX_ENTRIES + dm::MG_TILE - 1) / dm::MG_TILE;
+static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocTiles + 1];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint64_t* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" dm_status dm_merge_dicts_noalloc(uint32_t w, const void* main_dict, uint64_t m, const void* ud,
+                                            const uint32_t* perm, uint64_t d, void* new_dict, uint32_t* x_main,
+                                            uint32_t* x_delta, uint64_t* d_u, uint32_t* d_bits,
+                                            uint32_t* d_status, void* stream) {
+  if ((w != 4 && w != 8 && w != 16) || !d_u || !d_bits) return DM_EINVAL;
+  if (m + d > DM_NOALLOC_MAX_ENTRIES) return DM_EINVAL;
+  if ((m && (!main_dict || !x_main)) || (d && (!ud || !perm || !x_delta)) || (m + d && !new_dict)) return DM_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DM_ECUDA;
+  uint64_t* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) return DM_ECUDA;
+      g_noalloc_addr[dev] = static_cast<uint64_t*>(p);
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (m + d == 0) {
+    if (cudaMemsetAsync(d_u, 0, 8, s) != cudaSuccess || cudaMemsetAsync(d_bits, 0, 4, s) != cudaSuccess)
+      return DM_ECUDA;
+    return DM_OK;
+  }
+  const uint32_t tiles = dm::merge_tiles(m + d);
+  // look-back words and tile counter must start at zero; the array keeps
+  // whatever the previous call left
+  if (cudaMemsetAsync(scratch, 0, (size_t)(tiles + 1) * sizeof(uint64_t), s) != cudaSuccess) return DM_ECUDA;
+  dm::MergeArgs a{};
+  a.a = main_dict;
+  a.m = m;
+  a.b = ud;
+  a.perm = perm;
+  a.b_slot = nullptr;
+  a.d = d;
+  a.unew = new_dict;
+  a.xm = x_main;
+  a.xd = x_delta;
+  a.d_u = d_u;
+  a.d_bits = d_bits;
+  a.lookback = scratch;
+  a.counter = reinterpret_cast<uint32_t*>(scratch + tiles);
+  a.ntiles = tiles;
+  a.status = d_status;
+  uint64_t launches = 0;
+  return dm::launch_merge(w, a, s, &launches) == cudaSuccess ? DM_OK : DM_ECUDA;
+}

@@ -33,7 +33,7 @@ EXPORTS = [
     "dm_max_bits", "dm_scratch_bytes", "dm_merge_column", "dm_merge_table",
     "dm_table_scratch_bytes", "dm_merge_column_host", "dm_host_scratch_bytes", "dm_sort_delta",
     "dm_merge_dicts", "dm_reencode", "dm_sync_status", "dm_last_timing", "dm_timing_sum",
-    "dm_launch_count",
+    "dm_launch_count", "dm_merge_dicts_noalloc",
     "dm_status_str",
 ]
 
@@ -117,6 +117,8 @@ def _load():
             "dm_timing_sum": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(u32)], i32),
             "dm_launch_count": ([vp], u64),
             "dm_status_str": ([i32], ctypes.c_char_p),
+            "dm_merge_dicts_noalloc": ([u32, vp, u64, vp, vp, u64, vp, vp, vp, vp, vp, vp, vp],
+                                       i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -255,6 +257,19 @@ def dm_merge_dicts(ctx: Context, w: int, main_dict, m: int, ud, perm, d: int, ne
     _check(_load().dm_merge_dicts(ctx.handle, w, _ptr(main_dict), m, _ptr(ud), _ptr(perm), d,
                                   _ptr(new_dict), _ptr(x_main), _ptr(x_delta), _ptr(d_u),
                                   _ptr(d_bits), _stream(stream)), "dm_merge_dicts")
+
+
+def dm_merge_dicts_noalloc(w: int, main_dict, m: int, ud, perm, d: int, new_dict, x_main,
+                           x_delta, d_u, d_bits, d_status=None, stream=None):
+    """Step 1(b) + 2(a) with scratch in the library's static device memory
+    (no context, no allocation); m + d <= DM_NOALLOC_MAX_ENTRIES."""
+    _check(_load().dm_merge_dicts_noalloc(w, _ptr(main_dict), m, _ptr(ud), _ptr(perm), d,
+                                          _ptr(new_dict), _ptr(x_main), _ptr(x_delta), _ptr(d_u),
+                                          _ptr(d_bits), _ptr(d_status), _stream(stream)),
+           "dm_merge_dicts_noalloc")
+
+
+DM_NOALLOC_MAX_ENTRIES = 1 << 24
 
 
 def dm_reencode(ctx: Context, main_packed, main_bits: int, n_main: int, delta_codes, n_delta: int,
