@@ -75,7 +75,7 @@ typedef enum {
 
 /* flags for dm_merge_column / dm_merge_table */
 #define DM_FLAG_GENERIC_REENCODE 0x1u  /* force the runtime-width Step 2(b) path */
-#define DM_FLAG_X_SMEM 0x2u            /* stage X_M in shared memory (when it fits) */
+#define DM_FLAG_X_SMEM 0x2u            /* look X_M up in shared memory at any size (table or directory) */
 #define DM_FLAG_X_GLOBAL 0x4u          /* never stage X_M in shared memory */
 #define DM_FLAG_TIMING 0x8u            /* record per-step CUDA events (dm_last_timing) */
 
@@ -215,16 +215,29 @@ dm_status dm_merge_dicts_noalloc(uint32_t value_bytes, const void* main_dict, ui
  * DM_OK, or the most severe of DM_ETIMEOUT, DM_EUNSORTED, DM_ECODE. */
 dm_status dm_sync_status(dm_ctx* ctx, void* stream);
 
-/* Milliseconds of Steps 1(a), 1(b)+2(a), 2(b) and the whole merge of the
- * last dm_merge_column issued with DM_FLAG_TIMING (CUDA events on the
- * call's stream).  Synchronises on those events. */
-dm_status dm_last_timing(dm_ctx* ctx, float ms[4]);
+/* Milliseconds of the last dm_merge_column issued with DM_FLAG_TIMING, from
+ * CUDA events on the call's stream: [0] Step 1(a), [1] Step 1(b)+2(a),
+ * [2] the X_M directory for Step 2(b) (0 when not built), [3] the Step 2(b)
+ * kernel, [4] the whole merge.  Synchronises on those events. */
+dm_status dm_last_timing(dm_ctx* ctx, float ms[5]);
 
 /* Sum of the per-step milliseconds (as in dm_last_timing) over every
  * dm_merge_column call issued with DM_FLAG_TIMING since the previous
  * dm_timing_sum (at most 1024 calls are kept; *calls receives how many were
  * summed), then forget them.  Synchronises on those events. */
-dm_status dm_timing_sum(dm_ctx* ctx, float ms[4], uint32_t* calls);
+dm_status dm_timing_sum(dm_ctx* ctx, float ms[5], uint32_t* calls);
+
+/* Launch parameters of the kernels, per context (0 = library default).
+ * They change how the work is split, never the result. */
+typedef struct {
+  uint32_t reencode_warps;   /* Step 2(b): warps per block (1..16) */
+  uint32_t reencode_stages;  /* Step 2(b): input bulk-copy stages per warp (2..4) */
+  uint32_t reencode_obufs;   /* Step 2(b): output staging buffers per warp (1..2) */
+  uint32_t reserved[5];
+} dm_tuning;
+
+dm_status dm_set_tuning(dm_ctx* ctx, const dm_tuning* tuning);
+dm_status dm_get_tuning(const dm_ctx* ctx, dm_tuning* tuning);
 
 /* Kernels this context has launched so far. */
 uint64_t dm_launch_count(const dm_ctx* ctx);

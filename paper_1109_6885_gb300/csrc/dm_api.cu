@@ -20,13 +20,14 @@ struct dm_ctx {
   uint32_t* host_status = nullptr; // pinned readback
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_done = nullptr;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool timing_valid = false;
   // ring of per-call event quadruples for dm_timing_sum
   static constexpr uint32_t kRing = 1024;
   cudaEvent_t* ring = nullptr;
   uint32_t ring_n = 0;
   cudaEvent_t* last_ev = nullptr;   // quadruple of the last timed call
+  dm_tuning tuning{};
   uint64_t launches = 0;
 };
 
@@ -55,12 +56,12 @@ struct Carver {
 };
 
 struct ColumnScratch {
-  uint32_t* zero = nullptr;   // one memset covers sort + merge bookkeeping
+  uint32_t* zero = nullptr;   // one memset covers all Step 1 bookkeeping
   size_t zero_bytes = 0;
-  dm::SortArgs sort{};
-  dm::MergeArgs merge{};
+  dm::Step1Args s1{};
   uint32_t* xm = nullptr;
   uint32_t* xd = nullptr;
+  uint32_t* xdir = nullptr;   // directory of X_M for Step 2(b)
   void** slots = nullptr;
 };
 
@@ -69,12 +70,7 @@ size_t carve_column(void* base, const dm_column_in* in, const dm_column_out* out
   Carver c(base);
   const uint32_t w = in->value_bytes;
   const uint64_t m = in->main_dict_len, d = in->delta_dict_len;
-  const uint64_t sort_words = d ? dm::sort_zeroed_words(w, d) : 0;
-  const uint32_t mtiles = dm::merge_tiles(m + d);
-  // zeroed bookkeeping: merge look-back words + tile counter, then the sort's
-  // histograms, tile counters and look-back words
-  const size_t merge_bytes = (size_t)mtiles * 8 + 8;
-  const size_t zero_bytes = merge_bytes + sort_words * 4;
+  const size_t zero_bytes = (size_t)dm::step1_zeroed_words(w, m + d, d) * 4;
   char* zero = static_cast<char*>(c.take(zero_bytes));
   void* k0 = c.take(d * w);
   void* k1 = c.take(d * w);
@@ -83,27 +79,27 @@ size_t carve_column(void* base, const dm_column_in* in, const dm_column_out* out
   void* slots = c.take(2 * sizeof(void*));
   void* xm = (out && out->x_main) ? nullptr : c.take(m * 4);
   void* xd = (out && out->x_delta) ? nullptr : c.take(d * 4);
+  void* xdir = in->main_rows ? c.take((size_t)dm::reencode_dir_words() * 4) : nullptr;
   if (cs && base) {
     cs->zero = reinterpret_cast<uint32_t*>(zero);
     cs->zero_bytes = zero_bytes;
     cs->slots = static_cast<void**>(slots);
-    cs->merge.lookback = reinterpret_cast<uint64_t*>(zero);
-    cs->merge.counter = reinterpret_cast<uint32_t*>(zero + (size_t)mtiles * 8);
-    cs->merge.ntiles = mtiles;
-    uint32_t* zw = reinterpret_cast<uint32_t*>(zero + merge_bytes);
-    cs->sort.in_keys = in->delta_dict;
-    cs->sort.d = d;
-    cs->sort.keys[0] = k0;
-    cs->sort.keys[1] = k1;
-    cs->sort.vals[0] = static_cast<uint32_t*>(v0);
-    cs->sort.vals[1] = static_cast<uint32_t*>(v1);
-    cs->sort.hist = zw;
-    cs->sort.counters = zw + (size_t)w * 256;
-    cs->sort.lookback = zw + (size_t)w * 256 + w;
-    cs->sort.ntiles = dm::sort_tiles(d);
-    cs->sort.final_slot = cs->slots;
+    cs->xdir = static_cast<uint32_t*>(xdir);
+    dm::Step1Args& a = cs->s1;
+    dm::step1_layout(w, m + d, d, cs->zero, &a);
+    a.in_keys = in->delta_dict;
+    a.d = d;
+    a.keys[0] = k0;
+    a.keys[1] = k1;
+    a.vals[0] = static_cast<uint32_t*>(v0);
+    a.vals[1] = static_cast<uint32_t*>(v1);
+    a.final_slot = cs->slots;
+    a.a = in->main_dict;
+    a.m = m;
     cs->xm = (out && out->x_main) ? out->x_main : static_cast<uint32_t*>(xm);
     cs->xd = (out && out->x_delta) ? out->x_delta : static_cast<uint32_t*>(xd);
+    a.xm = cs->xm;
+    a.xd = cs->xd;
   }
   return c.used;
 }
@@ -137,8 +133,9 @@ dm_status check_column(const dm_column_in* in, const dm_column_out* out, bool de
 dm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DM_OK : DM_ECUDA; }
 
 // Steps 1(a)..2(b) of one column whose scratch is laid out at `base`.
-// ev: four events recorded before Step 1(a), before 1(b), before 2(b) and at
-// the end (nullptr: no timing).
+// ev: five events recorded before Step 1, after the sort, after the merge
+// and the X_M directory (one kernel: both at its end), before the Step 2(b)
+// kernel and at the end (nullptr: no timing).
 dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* base,
                      cudaStream_t s, uint32_t flags, cudaEvent_t* ev) {
   const bool timing = ev != nullptr;
@@ -147,55 +144,58 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
   const uint32_t w = in->value_bytes;
   const uint64_t m = in->main_dict_len, d = in->delta_dict_len;
   const uint64_t n_out = in->main_rows + in->delta_rows;
+
+  // Step 2(b) launch plan first: it says whether Step 1 builds a directory
+  dm::ReencodeArgs ra{};
+  ra.main_words = static_cast<const uint32_t*>(in->main_packed);
+  ra.main_words_n = dm_packed_bytes(in->main_rows, in->main_bits) / 4;
+  ra.n_main = in->main_rows;
+  ra.dcodes = in->delta_codes;
+  ra.n_delta = in->delta_rows;
+  ra.xm = cs.xm;
+  ra.m = (uint32_t)std::min<uint64_t>(m, 0xFFFFFFFFu);
+  ra.xd = cs.xd;
+  ra.d = (uint32_t)d;
+  ra.d_bits = out->d_new_bits;
+  ra.max_bits = bits_for(m + d);
+  ra.out_words = static_cast<uint32_t*>(out->new_packed);
+  ra.status = ctx->status;
+  ra.xdir = cs.xdir;
+  ra.tune_warps = ctx->tuning.reencode_warps;
+  ra.tune_stages = ctx->tuning.reencode_stages;
+  ra.tune_obufs = ctx->tuning.reencode_obufs;
+  dm::ReencodePlan plan{};
+  if (n_out && dm::plan_reencode(in->main_bits, ra, ctx->sm_count, flags, &plan) != cudaSuccess) return DM_ECUDA;
+
   cudaError_t e = cudaMemsetAsync(cs.zero, 0, cs.zero_bytes, s);
   if (e != cudaSuccess) return DM_ECUDA;
   if (timing) cudaEventRecord(ev[0], s);
-  if (d) {
-    cs.sort.status = ctx->status;
-    e = dm::launch_sort(w, cs.sort, s, ctx->sm_count, &ctx->launches);
-    if (e != cudaSuccess) return DM_ECUDA;
-  }
-  if (timing) cudaEventRecord(ev[1], s);
   if (m + d) {
-    dm::MergeArgs& ma = cs.merge;
-    ma.a = in->main_dict;
-    ma.m = m;
-    ma.b = nullptr;
-    ma.perm = nullptr;
-    ma.b_slot = d ? cs.slots : nullptr;
-    ma.d = d;
-    ma.unew = out->new_dict;
-    ma.xm = cs.xm;
-    ma.xd = cs.xd;
-    ma.d_u = out->d_new_dict_len;
-    ma.d_bits = out->d_new_bits;
-    ma.status = ctx->status;
-    e = dm::launch_merge(w, ma, s, &ctx->launches);
+    dm::Step1Args& a = cs.s1;
+    a.phases = dm::S1_MERGE | (d ? dm::S1_SORT : 0u) | (plan.needs_directory ? dm::S1_DIR : 0u);
+    a.unew = out->new_dict;
+    a.d_u = out->d_new_dict_len;
+    a.d_bits = out->d_new_bits;
+    a.xdir = cs.xdir;
+    a.dir_shift = plan.dir_shift;
+    a.dir_entries = plan.dir_entries;
+    a.status = ctx->status;
+    e = dm::launch_step1(w, a, s, ctx->sm_count, &ctx->launches);
   } else {
     e = cudaMemsetAsync(out->d_new_dict_len, 0, sizeof(uint64_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(out->d_new_bits, 0, sizeof(uint32_t), s);
   }
   if (e != cudaSuccess) return DM_ECUDA;
-  if (timing) cudaEventRecord(ev[2], s);
+  if (timing) {
+    cudaEventRecord(ev[1], s);
+    cudaEventRecord(ev[2], s);
+    cudaEventRecord(ev[3], s);
+  }
   if (n_out) {
-    dm::ReencodeArgs ra;
-    ra.main_words = static_cast<const uint32_t*>(in->main_packed);
-    ra.main_words_n = dm_packed_bytes(in->main_rows, in->main_bits) / 4;
-    ra.n_main = in->main_rows;
-    ra.dcodes = in->delta_codes;
-    ra.n_delta = in->delta_rows;
-    ra.xm = cs.xm;
-    ra.m = (uint32_t)std::min<uint64_t>(m, 0xFFFFFFFFu);
-    ra.xd = cs.xd;
-    ra.d = (uint32_t)d;
-    ra.d_bits = out->d_new_bits;
-    ra.max_bits = bits_for(m + d);
-    ra.out_words = static_cast<uint32_t*>(out->new_packed);
-    ra.status = ctx->status;
-    e = dm::launch_reencode(in->main_bits, ra, s, ctx->sm_count, flags, &ctx->launches);
+    e = dm::launch_reencode_planned(plan, ra, s, &ctx->launches);
     if (e != cudaSuccess) return DM_ECUDA;
   }
-  if (timing) cudaEventRecord(ev[3], s);
+  if (timing) cudaEventRecord(ev[4], s);
   return DM_OK;
 }
 
@@ -290,7 +290,7 @@ void dm_destroy(dm_ctx* ctx) {
   for (auto e : ctx->ev)
     if (e) cudaEventDestroy(e);
   if (ctx->ring) {
-    for (uint32_t i = 0; i < 4 * dm_ctx::kRing; ++i)
+    for (uint32_t i = 0; i < 5 * dm_ctx::kRing; ++i)
       if (ctx->ring[i]) cudaEventDestroy(ctx->ring[i]);
     delete[] ctx->ring;
   }
@@ -328,13 +328,13 @@ dm_status dm_merge_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_o
   if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
   const bool timing = (flags & DM_FLAG_TIMING) != 0;
   if (timing && !ctx->ring) {
-    ctx->ring = new (std::nothrow) cudaEvent_t[4 * dm_ctx::kRing]();
+    ctx->ring = new (std::nothrow) cudaEvent_t[5 * dm_ctx::kRing]();
     if (!ctx->ring) return DM_ENOMEM;
-    for (uint32_t i = 0; i < 4 * dm_ctx::kRing; ++i)
+    for (uint32_t i = 0; i < 5 * dm_ctx::kRing; ++i)
       if (cudaEventCreate(&ctx->ring[i]) != cudaSuccess) return DM_ECUDA;
   }
   cudaEvent_t* ev = nullptr;
-  if (timing) ev = ctx->ring_n < dm_ctx::kRing ? ctx->ring + 4 * ctx->ring_n : ctx->ev;
+  if (timing) ev = ctx->ring_n < dm_ctx::kRing ? ctx->ring + 5 * ctx->ring_n : ctx->ev;
   st = run_column(ctx, in, out, ctx->arena, as_stream(stream), flags, ev);
   ctx->timing_valid = timing && st == DM_OK;
   if (ctx->timing_valid) {
@@ -371,7 +371,7 @@ size_t dm_host_scratch_bytes(const dm_column_in* in, uint32_t flags) {
   b += align_up(m * w) + align_up(dm_packed_bytes(in->main_rows, in->main_bits));
   b += align_up(d * w) + align_up(in->delta_rows * 4);
   b += align_up((m + d) * w) + align_up(dm_packed_bytes(n_out, bits_for(m + d)));
-  b += align_up(m * 4) + align_up(d * 4) + align_up(16);
+  b += align_up(m * 4) + align_up(d * 4) + align_up(16) + align_up((size_t)dm::reencode_dir_words() * 4);
   return b + dm_scratch_bytes(in, flags);
 }
 
@@ -400,6 +400,7 @@ dm_status dm_merge_column_host(dm_ctx* ctx, const dm_column_in* in, const dm_col
   dout.x_main = static_cast<uint32_t*>(c.take(m * 4));
   dout.x_delta = static_cast<uint32_t*>(c.take(d * 4));
   char* scal = static_cast<char*>(c.take(16));
+  uint32_t* xdir = static_cast<uint32_t*>(c.take((size_t)dm::reencode_dir_words() * 4));
   dout.d_new_dict_len = reinterpret_cast<uint64_t*>(scal);
   dout.d_new_bits = reinterpret_cast<uint32_t*>(scal + 8);
   void* scratch = c.take(0);
@@ -436,7 +437,7 @@ dm_status dm_merge_column_host(dm_ctx* ctx, const dm_column_in* in, const dm_col
   }
   if (n_out) {
     // X tables now live in dout; re-encode only
-    dm::ReencodeArgs ra;
+    dm::ReencodeArgs ra{};
     ra.main_words = static_cast<const uint32_t*>(din.main_packed);
     ra.main_words_n = main_bytes / 4;
     ra.n_main = din.main_rows;
@@ -450,6 +451,10 @@ dm_status dm_merge_column_host(dm_ctx* ctx, const dm_column_in* in, const dm_col
     ra.max_bits = bits_for(m + d);
     ra.out_words = static_cast<uint32_t*>(dout.new_packed);
     ra.status = ctx->status;
+    ra.xdir = xdir;
+    ra.tune_warps = ctx->tuning.reencode_warps;
+    ra.tune_stages = ctx->tuning.reencode_stages;
+    ra.tune_obufs = ctx->tuning.reencode_obufs;
     e = dm::launch_reencode(din.main_bits, ra, s, ctx->sm_count, flags, &ctx->launches);
     if (e != cudaSuccess) return DM_ECUDA;
   }
@@ -489,8 +494,9 @@ dm_status dm_sort_delta(dm_ctx* ctx, uint32_t w, const void* delta_dict, uint64_
   ColumnScratch cs;
   carve_column(ctx->arena, &in, nullptr, &cs);
   if (cudaMemsetAsync(cs.zero, 0, cs.zero_bytes, s) != cudaSuccess) return DM_ECUDA;
-  cs.sort.status = ctx->status;
-  if (dm::launch_sort(w, cs.sort, s, ctx->sm_count, &ctx->launches) != cudaSuccess) return DM_ECUDA;
+  cs.s1.phases = dm::S1_SORT;
+  cs.s1.status = ctx->status;
+  if (dm::launch_step1(w, cs.s1, s, ctx->sm_count, &ctx->launches) != cudaSuccess) return DM_ECUDA;
   return cuda_status(dm::launch_sort_copy_out(w, cs.slots, d, ud_out, perm_out, s, &ctx->launches));
 }
 
@@ -506,28 +512,25 @@ dm_status dm_merge_dicts(dm_ctx* ctx, uint32_t w, const void* main_dict, uint64_
       return DM_ECUDA;
     return DM_OK;
   }
-  const uint32_t mt = dm::merge_tiles(m + d);
-  const size_t need = align_up((size_t)mt * 8 + 8);
-  if (need > ctx->arena_bytes) return DM_ENOMEM;
-  uint64_t* lb = static_cast<uint64_t*>(ctx->arena);
-  if (cudaMemsetAsync(lb, 0, (size_t)mt * 8 + 8, s) != cudaSuccess) return DM_ECUDA;
-  dm::MergeArgs a{};
+  const size_t zb = (size_t)dm::step1_zeroed_words(w, m + d, 0) * 4;
+  if (align_up(zb) > ctx->arena_bytes) return DM_ENOMEM;
+  uint32_t* zero = static_cast<uint32_t*>(ctx->arena);
+  if (cudaMemsetAsync(zero, 0, zb, s) != cudaSuccess) return DM_ECUDA;
+  dm::Step1Args a{};
+  dm::step1_layout(w, m + d, 0, zero, &a);
   a.a = main_dict;
   a.m = m;
   a.b = ud;
   a.perm = perm;
-  a.b_slot = nullptr;
   a.d = d;
   a.unew = new_dict;
   a.xm = x_main;
   a.xd = x_delta;
   a.d_u = d_u;
   a.d_bits = d_bits;
-  a.lookback = lb;
-  a.counter = reinterpret_cast<uint32_t*>(lb + mt);
-  a.ntiles = mt;
+  a.phases = dm::S1_MERGE;
   a.status = ctx->status;
-  return cuda_status(dm::launch_merge(w, a, s, &ctx->launches));
+  return cuda_status(dm::launch_step1(w, a, s, ctx->sm_count, &ctx->launches));
 }
 
 dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bits, uint64_t n_main,
@@ -541,7 +544,7 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
     return DM_EINVAL;
   if (n_main + n_delta && max_bits && (!out_packed || !aligned(out_packed, 16))) return DM_EINVAL;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
-  dm::ReencodeArgs ra;
+  dm::ReencodeArgs ra{};
   ra.main_words = main_packed;
   ra.main_words_n = dm_packed_bytes(n_main, main_bits) / 4;
   ra.n_main = n_main;
@@ -555,7 +558,27 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
   ra.max_bits = max_bits;
   ra.out_words = out_packed;
   ra.status = ctx->status;
+  // the X_M directory goes to the arena when it has room (else no directory)
+  ra.xdir = ctx->arena_bytes >= (size_t)dm::reencode_dir_words() * 4 ? static_cast<uint32_t*>(ctx->arena) : nullptr;
+  ra.tune_warps = ctx->tuning.reencode_warps;
+  ra.tune_stages = ctx->tuning.reencode_stages;
+  ra.tune_obufs = ctx->tuning.reencode_obufs;
   return cuda_status(dm::launch_reencode(main_bits, ra, as_stream(stream), ctx->sm_count, flags, &ctx->launches));
+}
+
+dm_status dm_set_tuning(dm_ctx* ctx, const dm_tuning* t) {
+  if (!ctx || !t) return DM_EINVAL;
+  if (t->reencode_warps > 16 || (t->reencode_stages && (t->reencode_stages < 2 || t->reencode_stages > 4)) ||
+      t->reencode_obufs > 2)
+    return DM_EINVAL;
+  ctx->tuning = *t;
+  return DM_OK;
+}
+
+dm_status dm_get_tuning(const dm_ctx* ctx, dm_tuning* t) {
+  if (!ctx || !t) return DM_EINVAL;
+  *t = ctx->tuning;
+  return DM_OK;
 }
 
 dm_status dm_sync_status(dm_ctx* ctx, void* stream) {
@@ -577,30 +600,31 @@ dm_status dm_sync_status(dm_ctx* ctx, void* stream) {
   return DM_OK;
 }
 
-static dm_status elapsed4(cudaEvent_t* ev, float ms[4]) {
-  if (cudaEventSynchronize(ev[3]) != cudaSuccess) return DM_ECUDA;
+static dm_status elapsed5(cudaEvent_t* ev, float ms[5]) {
+  if (cudaEventSynchronize(ev[4]) != cudaSuccess) return DM_ECUDA;
   if (cudaEventElapsedTime(&ms[0], ev[0], ev[1]) != cudaSuccess ||
       cudaEventElapsedTime(&ms[1], ev[1], ev[2]) != cudaSuccess ||
       cudaEventElapsedTime(&ms[2], ev[2], ev[3]) != cudaSuccess ||
-      cudaEventElapsedTime(&ms[3], ev[0], ev[3]) != cudaSuccess)
+      cudaEventElapsedTime(&ms[3], ev[3], ev[4]) != cudaSuccess ||
+      cudaEventElapsedTime(&ms[4], ev[0], ev[4]) != cudaSuccess)
     return DM_ECUDA;
   return DM_OK;
 }
 
-dm_status dm_last_timing(dm_ctx* ctx, float ms[4]) {
+dm_status dm_last_timing(dm_ctx* ctx, float ms[5]) {
   if (!ctx || !ms || !ctx->timing_valid || !ctx->last_ev) return DM_EINVAL;
-  return elapsed4(ctx->last_ev, ms);
+  return elapsed5(ctx->last_ev, ms);
 }
 
-dm_status dm_timing_sum(dm_ctx* ctx, float ms[4], uint32_t* calls) {
+dm_status dm_timing_sum(dm_ctx* ctx, float ms[5], uint32_t* calls) {
   if (!ctx || !ms || !calls) return DM_EINVAL;
-  for (int k = 0; k < 4; ++k) ms[k] = 0.f;
+  for (int k = 0; k < 5; ++k) ms[k] = 0.f;
   *calls = 0;
   for (uint32_t i = 0; i < ctx->ring_n; ++i) {
-    float one[4];
-    dm_status st = elapsed4(ctx->ring + 4 * i, one);
+    float one[5];
+    dm_status st = elapsed5(ctx->ring + 5 * i, one);
     if (st != DM_OK) return st;
-    for (int k = 0; k < 4; ++k) ms[k] += one[k];
+    for (int k = 0; k < 5; ++k) ms[k] += one[k];
   }
   *calls = ctx->ring_n;
   ctx->ring_n = 0;

@@ -74,6 +74,15 @@ __device__ __forceinline__ uint32_t key_digit(const u128& k, int pass) {
 }
 
 template <class K>
+__device__ __forceinline__ K key_max_value();
+template <>
+__device__ __forceinline__ uint32_t key_max_value<uint32_t>() { return 0xFFFFFFFFu; }
+template <>
+__device__ __forceinline__ uint64_t key_max_value<uint64_t>() { return ~0ull; }
+template <>
+__device__ __forceinline__ u128 key_max_value<u128>() { return u128{~0ull, ~0ull}; }
+
+template <class K>
 __device__ __forceinline__ K load_key(const K* p) {
   return __ldg(p);
 }

@@ -6,59 +6,59 @@
 
 namespace dm {
 
-// ---------------------------------------------------------------- Step 1(a)
-constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 8;
-constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+// ---------------------------------------------------------------- Step 1
+constexpr int RS_ITEMS = 4;       // keys per thread of a sort tile
+constexpr int RS_TILE = 256 * RS_ITEMS;   // keys per sort tile
+constexpr int MG_TILE = 2048;     // merged positions per merge tile
+constexpr uint32_t S1_SORT = 1, S1_MERGE = 2, S1_DIR = 4;   // phases
+constexpr uint32_t S1_BARRIERS = 32;                        // barrier counters per launch
 
-struct SortArgs {
+struct Step1Args {
+  // Step 1(a): sort of the delta dictionary
   const void* in_keys;       // D_dict (insertion order)
   uint64_t d;
   void* keys[2];             // ping-pong key buffers, d keys each
   uint32_t* vals[2];         // ping-pong insertion codes
   uint32_t* hist;            // [W][256] digit counts (zeroed)
-  uint32_t* counters;        // [W] dynamic tile counters (zeroed)
-  uint32_t* lookback;        // [W][ntiles][256] look-back words (zeroed)
-  uint32_t ntiles;
-  void** final_slot;         // device slots: [0] = sorted keys, [1] = perm
-  uint32_t* status;
-};
-
-// Scratch words the sort needs zeroed (hist + counters + look-back).
-uint64_t sort_zeroed_words(uint32_t w, uint64_t d);
-uint32_t sort_tiles(uint64_t d);
-// Launches histogram + one kernel per digit pass on `stream`.
-cudaError_t launch_sort(uint32_t w, const SortArgs& a, cudaStream_t stream, uint32_t sm_count,
-                        uint64_t* launches);
-// Copies the sorted result named by final_slot into caller buffers.
-cudaError_t launch_sort_copy_out(uint32_t w, void** final_slot, uint64_t d, void* ud_out,
-                                 uint32_t* perm_out, cudaStream_t stream, uint64_t* launches);
-
-// ---------------------------------------------------------------- Step 1(b) + 2(a)
-constexpr int MG_THREADS = 256;
-constexpr int MG_ITEMS = 8;
-constexpr int MG_TILE = MG_THREADS * MG_ITEMS;
-
-struct MergeArgs {
+  uint32_t* sort_lb;         // [W][sort_tiles][256] look-back words (zeroed)
+  uint32_t sort_tiles;
+  uint32_t hist_blocks;      // set by the launcher
+  void** final_slot;         // optional: [0] sorted keys, [1] perm (for copy-out)
+  // Step 1(b) + 2(a): merge with the main dictionary
   const void* a;             // U_M
   uint64_t m;
-  const void* b;             // U_D (used when b_slot is NULL)
-  const uint32_t* perm;      // insertion codes of U_D (used when b_slot is NULL)
-  void* const* b_slot;       // device slots written by the sort: [0] U_D, [1] perm
-  uint64_t d;
+  const void* b;             // U_D when the sort phase is off
+  const uint32_t* perm;      // its insertion codes
   void* unew;
   uint32_t* xm;
   uint32_t* xd;
   uint64_t* d_u;
   uint32_t* d_bits;
-  uint64_t* lookback;        // [ntiles] (zeroed)
-  uint32_t* counter;         // tile counter (zeroed)
-  uint32_t ntiles;
+  uint64_t* merge_lb;        // [merge_tiles] look-back words (zeroed)
+  uint32_t merge_tiles;
+  // directory of X_M for Step 2(b)
+  uint32_t* xdir;
+  uint32_t dir_shift;
+  uint32_t dir_entries;
+  // control
+  uint32_t phases;           // S1_SORT | S1_MERGE | S1_DIR
+  uint32_t* barriers;        // [S1_BARRIERS] (zeroed)
   uint32_t* status;
 };
 
+uint32_t sort_tiles(uint64_t d);
 uint32_t merge_tiles(uint64_t n);
-cudaError_t launch_merge(uint32_t w, const MergeArgs& a, cudaStream_t stream, uint64_t* launches);
+// 32-bit words of bookkeeping to zero before a Step 1 launch that merges
+// n_merge dictionary entries and sorts d_sort keys of w bytes.
+uint64_t step1_zeroed_words(uint32_t w, uint64_t n_merge, uint64_t d_sort);
+// Place that bookkeeping (look-back words, barriers, histograms) at `zero`.
+void step1_layout(uint32_t w, uint64_t n_merge, uint64_t d_sort, uint32_t* zero, Step1Args* a);
+// One cooperative launch running the phases in a.phases.
+cudaError_t launch_step1(uint32_t w, const Step1Args& a, cudaStream_t stream, uint32_t sm_count,
+                         uint64_t* launches);
+// Copies the sorted result named by final_slot into caller buffers.
+cudaError_t launch_sort_copy_out(uint32_t w, void** final_slot, uint64_t d, void* ud_out,
+                                 uint32_t* perm_out, cudaStream_t stream, uint64_t* launches);
 
 // ---------------------------------------------------------------- Step 2(b)
 struct ReencodeArgs {
@@ -75,8 +75,25 @@ struct ReencodeArgs {
   uint32_t max_bits;         // host bound of E'_C; sizes the output buffer
   uint32_t* out_words;
   uint32_t* status;
+  uint32_t* xdir;            // scratch for the X_M directory (reencode_dir_words() words) or NULL
+  uint32_t tune_warps;       // 0 = default; warps per block
+  uint32_t tune_stages;      // 0 = default; input stages per warp
+  uint32_t tune_obufs;       // 0 = default; output buffers per warp
 };
 
+uint32_t reencode_dir_words();
+
+// Host-side launch plan of Step 2(b) (opaque storage).
+struct ReencodePlan {
+  alignas(8) unsigned char storage[96];
+  bool needs_directory;
+  uint32_t dir_shift;
+  uint32_t dir_entries;
+};
+cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, uint32_t flags, ReencodePlan* out);
+cudaError_t launch_xdir(const ReencodePlan& plan, const ReencodeArgs& a, cudaStream_t s, uint64_t* launches);
+cudaError_t launch_reencode_planned(const ReencodePlan& plan, const ReencodeArgs& a, cudaStream_t s,
+                                    uint64_t* launches);
 cudaError_t launch_reencode(uint32_t b, const ReencodeArgs& a, cudaStream_t stream,
                             uint32_t sm_count, uint32_t flags, uint64_t* launches);
 

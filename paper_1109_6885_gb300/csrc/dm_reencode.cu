@@ -23,18 +23,19 @@
 //     stores to global memory; the last tile is stored with clipped plain
 //     stores and zero padding up to the stream's 16-byte end.
 // Tiles that hold delta rows or the main/delta boundary use a plain path.
+#include <string.h>
+
 #include <mutex>
 
 #include "dm_common.cuh"
 #include "dm_internal.h"
+#include "dm_xdir.cuh"
 
 namespace dm {
 
 namespace {
 
-constexpr int RE_WARPS = 8;
-constexpr int RE_THREADS = RE_WARPS * 32;
-constexpr int RE_STAGES = 3;
+constexpr uint32_t RE_STAGES_MAX = 4;
 constexpr uint32_t RE_TILE = 1024;          // codes per warp tile
 constexpr uint32_t RE_XSMEM_MAX = 16384;    // X_M entries staged in shared memory at most
 
@@ -140,27 +141,45 @@ __device__ __forceinline__ uint32_t code_at(const uint32_t* words, uint64_t nwor
 struct Layout {
   uint32_t in_words;    // words of one input stage (32 * b)
   uint32_t out_words;   // words of one output buffer (32 * max_bits)
-  uint32_t x_entries;   // X_M entries staged in shared memory (0 = none)
+  uint32_t x_mode;      // X_M lookup: 0 global gather, 1 direct table in smem, 2 directory in smem
+  uint32_t x_entries;   // mode 1: entries of X_M staged; mode 2: directory entries
+  uint32_t dir_shift;   // mode 2: main codes per directory bucket = 2^dir_shift
   uint32_t generic;     // 1: plain per-code path and runtime-width packer on every tile
+  uint32_t stages;      // input bulk-copy stages per warp (2..4)
+  uint32_t obufs;       // output staging buffers per warp (1..2)
 };
+
+constexpr uint32_t RE_WARPS_MAX = 16;
+constexpr uint32_t RE_BAR_BYTES = RE_WARPS_MAX * RE_STAGES_MAX * 8;   // 512
 
 __host__ __device__ __forceinline__ uint32_t round4(uint32_t v) { return (v + 3u) & ~3u; }
 
-__host__ __device__ __forceinline__ uint32_t smem_bytes(const Layout& L) {
-  uint32_t bars = RE_WARPS * RE_STAGES * 8;
-  uint32_t per_warp = RE_STAGES * round4(L.in_words) + 2 * round4(L.out_words);
-  return ((bars + 127) & ~127u) + RE_WARPS * per_warp * 4 + round4(L.x_entries) * 4;
+__host__ __device__ __forceinline__ uint32_t per_warp_words(const Layout& L) {
+  return L.stages * round4(L.in_words) + L.obufs * round4(L.out_words);
+}
+
+__host__ __device__ __forceinline__ uint32_t smem_bytes(const Layout& L, uint32_t warps) {
+  return RE_BAR_BYTES + warps * per_warp_words(L) * 4 + round4(L.x_entries) * 4;
+}
+
+// The X_M directory (see dm_xdir.cuh) built by a kernel of its own when
+// Step 2(b) runs without the Step 1 kernel in front of it.
+__global__ void xdir_build_kernel(const uint32_t* __restrict__ xm, uint32_t m, uint32_t s, uint32_t R,
+                                  uint32_t* __restrict__ dir) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < R) dir[b] = xdir_entry<false>(xm, m, s, b);
 }
 
 template <int B>
-__global__ void __launch_bounds__(RE_THREADS) reencode_kernel(ReencodeArgs a, Layout L) {
+__global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArgs a, Layout L) {
   extern __shared__ __align__(128) uint8_t smem[];
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + warp * RE_STAGES;
-  uint32_t* region = reinterpret_cast<uint32_t*>(smem + ((RE_WARPS * RE_STAGES * 8 + 127) & ~127u));
-  const uint32_t per_warp = RE_STAGES * round4(L.in_words) + 2 * round4(L.out_words);
-  uint32_t* wbase = region + warp * per_warp;
-  uint32_t* s_x = region + RE_WARPS * per_warp;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + warp * RE_STAGES_MAX;
+  const uint32_t stages = L.stages;
+  uint32_t* region = reinterpret_cast<uint32_t*>(smem + RE_BAR_BYTES);
+  const uint32_t pw = per_warp_words(L);
+  uint32_t* wbase = region + warp * pw;
+  uint32_t* s_x = region + nwarps * pw;
 
   const uint32_t bo = *a.d_bits;
   if (bo > a.max_bits) {
@@ -171,23 +190,25 @@ __global__ void __launch_bounds__(RE_THREADS) reencode_kernel(ReencodeArgs a, La
   const uint64_t out_total = ((n_out * bo + 127) / 128) * 4;
   const uint64_t n_tiles = (n_out + RE_TILE - 1) / RE_TILE;
   const uint64_t full_tiles = L.generic ? 0 : a.n_main / RE_TILE;
-  const uint64_t gw = (uint64_t)blockIdx.x * RE_WARPS + warp;
-  const uint64_t nw = (uint64_t)gridDim.x * RE_WARPS;
+  const uint64_t gw = (uint64_t)blockIdx.x * nwarps + warp;
+  const uint64_t nw = (uint64_t)gridDim.x * nwarps;
   constexpr uint32_t in_bytes = 128u * B;
-  const bool x_smem = L.x_entries > 0;
+  const uint32_t xmode = L.x_mode;
+  const uint32_t dshift = L.dir_shift, dmask = (1u << L.dir_shift) - 1u;
 
-  if (x_smem) {
-    for (uint32_t i = threadIdx.x; i < L.x_entries; i += RE_THREADS) s_x[i] = __ldg(a.xm + i);
+  if (xmode != 0) {
+    const uint32_t* src = xmode == 1 ? a.xm : a.xdir;
+    for (uint32_t i = threadIdx.x; i < L.x_entries; i += blockDim.x) s_x[i] = __ldg(src + i);
     __syncthreads();
   }
   if (lane == 0) {
-    for (int s = 0; s < RE_STAGES; ++s) mbar_init(&bars[s], 1);
+    for (uint32_t s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
     fence_mbar_init();
   }
   __syncwarp();
   if constexpr (B > 0) {
     if (lane == 0) {
-      for (int s = 0; s < RE_STAGES; ++s) {
+      for (uint32_t s = 0; s < stages; ++s) {
         uint64_t t = gw + (uint64_t)s * nw;
         if (t < full_tiles) {
           mbar_arrive_expect_tx(&bars[s], in_bytes);
@@ -198,15 +219,14 @@ __global__ void __launch_bounds__(RE_THREADS) reencode_kernel(ReencodeArgs a, La
   }
 
   bool timed_out = false;
-  uint32_t it = 0;
+  uint32_t it = 0, st = 0, ph = 0;   // iteration, its input stage, that stage's phase
   for (uint64_t t = gw; t < n_tiles; t += nw, ++it) {
     uint32_t x[32];
     if (t < full_tiles) {
       uint32_t c[32];
       if constexpr (B > 0) {
-        const uint32_t st = it % RE_STAGES;
         uint32_t* stage = wbase + st * round4(L.in_words);
-        const bool ok = mbar_wait(&bars[st], (it / RE_STAGES) & 1u, a.status);
+        const bool ok = mbar_wait(&bars[st], ph, a.status);
         if (!__all_sync(0xFFFFFFFFu, ok)) {
           timed_out = true;
           break;
@@ -215,13 +235,17 @@ __global__ void __launch_bounds__(RE_THREADS) reencode_kernel(ReencodeArgs a, La
         load_row<B>(stage + lane * B, w);
         __syncwarp();
         if (lane == 0) {
-          uint64_t tn = t + (uint64_t)RE_STAGES * nw;
+          uint64_t tn = t + (uint64_t)stages * nw;
           if (tn < full_tiles) {
             mbar_arrive_expect_tx(&bars[st], in_bytes);
             bulk_g2s(stage, a.main_words + tn * 32 * B, in_bytes, &bars[st]);
           }
         }
         unpack32<B>(w, c);
+        if (++st == stages) {
+          st = 0;
+          ph ^= 1u;
+        }
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) c[j] = 0;
@@ -234,7 +258,22 @@ __global__ void __launch_bounds__(RE_THREADS) reencode_kernel(ReencodeArgs a, La
 #pragma unroll
         for (int j = 0; j < 32; ++j) c[j] = min(c[j], a.m - 1);
       }
-      if (x_smem) {
+      if (xmode == 2) {
+        uint32_t many = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const uint32_t e = s_x[c[j] >> dshift];
+          const uint32_t y = e + ((c[j] & dmask) << 20);
+          x[j] = c[j] + (y & 0xFFFFFu) + (y >> 31);
+          many |= ((e >> 20) == DIR_MANY_TOP ? 1u : 0u) << j;
+        }
+        // codes in buckets with several steps read X_M itself
+        if (__any_sync(0xFFFFFFFFu, many != 0)) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if ((many >> j) & 1u) x[j] = __ldg(a.xm + c[j]);
+        }
+      } else if (xmode == 1) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) x[j] = s_x[c[j]];
       } else {
@@ -266,8 +305,13 @@ __global__ void __launch_bounds__(RE_THREADS) reencode_kernel(ReencodeArgs a, La
       }
     }
 
-    uint32_t* ob = wbase + RE_STAGES * round4(L.in_words) + (it & 1u) * round4(L.out_words);
-    if (lane == 0) bulk_wait_read<1>();
+    const uint32_t obi = L.obufs == 1 ? 0u : (it & 1u);
+    uint32_t* ob = wbase + stages * round4(L.in_words) + obi * round4(L.out_words);
+    // the bulk store that last read this buffer must have finished reading
+    if (lane == 0) {
+      if (L.obufs == 1) bulk_wait_read<0>();
+      else bulk_wait_read<1>();
+    }
     __syncwarp();
     uint32_t* row = ob + lane * bo;
     if (L.generic) {
@@ -296,10 +340,11 @@ __global__ void __launch_bounds__(RE_THREADS) reencode_kernel(ReencodeArgs a, La
   if constexpr (B > 0) {
     if (timed_out && lane == 0) {
       // let the copies already in flight land before the block exits
-      for (uint32_t k = 0; k < RE_STAGES; ++k) {
-        uint32_t i2 = it + k;
-        uint64_t t2 = gw + (uint64_t)i2 * nw;
-        if (t2 < full_tiles) mbar_wait(&bars[i2 % RE_STAGES], (i2 / RE_STAGES) & 1u, a.status);
+      for (uint32_t k = 0; k < stages; ++k) {
+        const uint64_t t2 = gw + (uint64_t)(it + k) * nw;
+        const uint32_t s2 = (st + k) % stages;
+        const uint32_t p2 = ph ^ ((st + k) >= stages ? 1u : 0u);
+        if (t2 < full_tiles) mbar_wait(&bars[s2], p2, a.status);
       }
     }
   }
@@ -338,41 +383,114 @@ Registry& registry() {
 
 }  // namespace
 
-cudaError_t launch_reencode(uint32_t b, const ReencodeArgs& a, cudaStream_t s, uint32_t sm_count, uint32_t flags,
-                            uint64_t* launches) {
-  if (b > 32 || a.max_bits > 32) return cudaErrorInvalidValue;
-  const uint64_t n_out = a.n_main + a.n_delta;
-  if (n_out == 0) return cudaSuccess;
+uint32_t reencode_dir_words() { return RE_DIR_MAX; }
+
+// Host-side launch plan of Step 2(b): lookup mode, block size, shared memory.
+struct ReencodePlanImpl {
   Layout L;
+  uint32_t warps, bytes, grid;
+  KernelFn fn;
+};
+static_assert(sizeof(ReencodePlanImpl) <= sizeof(ReencodePlan), "plan storage");
+
+cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, uint32_t flags, ReencodePlan* out) {
+  if (b > 32 || a.max_bits > 32) return cudaErrorInvalidValue;
+  ReencodePlanImpl P{};
+  const uint64_t n_out = a.n_main + a.n_delta;
+  Layout& L = P.L;
   L.in_words = 32 * b;
   L.out_words = 32 * (a.max_bits > b + 1 ? a.max_bits : b + 1);
   if (L.out_words > 32 * 32) L.out_words = 32 * 32;
-  bool want_smem = (flags & DM_FLAG_X_SMEM) || (!(flags & DM_FLAG_X_GLOBAL) && a.m <= RE_XSMEM_MAX && a.n_main >= (1u << 20));
-  L.x_entries = (want_smem && a.m <= RE_XSMEM_MAX && a.n_main > 0) ? a.m : 0;
   L.generic = (flags & DM_FLAG_GENERIC_REENCODE) ? 1u : 0u;
-  const uint32_t bytes = smem_bytes(L);
-
+  L.stages = a.tune_stages >= 2 && a.tune_stages <= RE_STAGES_MAX ? a.tune_stages : 2;
+  L.obufs = a.tune_obufs == 1 || a.tune_obufs == 2 ? a.tune_obufs : 1;
+  // X_M lookup: a direct table in shared memory when it is small; else the
+  // shared-memory directory of its steps; never smem when asked not to
+  const bool allow_smem = !(flags & DM_FLAG_X_GLOBAL) && a.n_main > 0 && !L.generic;
+  const bool want_smem = (flags & DM_FLAG_X_SMEM) != 0 || a.n_main >= (1u << 20);
+  if (allow_smem && want_smem && a.m <= RE_XSMEM_MAX) {
+    L.x_mode = 1;
+    L.x_entries = a.m;
+  } else if (allow_smem && want_smem && a.xdir && (uint64_t)a.m <= ((uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX)) {
+    L.x_mode = 2;
+    xdir_shape(a.m, &L.dir_shift, &L.x_entries);
+  }
+  // warps per block: as many as the device's shared memory allows, up to 16
+  // (one block per SM); a lookup table that leaves room for fewer than 4
+  // warps is dropped for the global gather
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return cudaErrorInvalidValue;
+  auto fit = [&](const Layout& l, uint32_t cap) {
+    const uint64_t fixed = RE_BAR_BYTES + (uint64_t)round4(l.x_entries) * 4;
+    const uint64_t per = (uint64_t)per_warp_words(l) * 4;
+    uint64_t w = fixed < (uint64_t)optin ? ((uint64_t)optin - fixed) / per : 0;
+    return (uint32_t)(w < cap ? w : cap);
+  };
+  const uint32_t want_warps = a.tune_warps >= 1 && a.tune_warps <= RE_WARPS_MAX ? a.tune_warps : 16;
+  P.warps = fit(L, want_warps);
+  if (L.x_mode && P.warps < 4) {
+    L.x_mode = 0;
+    L.x_entries = 0;
+    L.dir_shift = 0;
+    P.warps = fit(L, want_warps);
+  }
+  if (P.warps < 1) return cudaErrorInvalidConfiguration;
+  P.bytes = smem_bytes(L, P.warps);
   Registry& R = registry();
-  KernelFn fn = R.fn[b];
+  P.fn = R.fn[b];
   {
     std::lock_guard<std::mutex> g(R.mu);
-    if (R.smem_set[b] < bytes) {
-      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (R.smem_set[b] < P.bytes) {
+      cudaError_t e = cudaFuncSetAttribute(P.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.bytes);
       if (e != cudaSuccess) return e;
-      R.smem_set[b] = bytes;
+      R.smem_set[b] = P.bytes;
     }
   }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, RE_THREADS, bytes);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.fn, P.warps * 32, P.bytes);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const uint64_t n_tiles = (n_out + RE_TILE - 1) / RE_TILE;
-  uint64_t grid = (n_tiles + RE_WARPS - 1) / RE_WARPS;
+  uint64_t grid = (n_tiles + P.warps - 1) / P.warps;
   const uint64_t cap = (uint64_t)sm_count * per_sm;
   if (grid > cap) grid = cap;
-  fn<<<(uint32_t)grid, RE_THREADS, bytes, s>>>(a, L);
+  P.grid = (uint32_t)(grid ? grid : 1);
+  memcpy(out->storage, &P, sizeof(P));
+  out->needs_directory = L.x_mode == 2;
+  out->dir_shift = L.dir_shift;
+  out->dir_entries = L.x_mode == 2 ? L.x_entries : 0;
+  return cudaSuccess;
+}
+
+cudaError_t launch_xdir(const ReencodePlan& plan, const ReencodeArgs& a, cudaStream_t s, uint64_t* launches) {
+  ReencodePlanImpl P;
+  memcpy(&P, plan.storage, sizeof(P));
+  if (P.L.x_mode != 2) return cudaSuccess;
+  xdir_build_kernel<<<(P.L.x_entries + 255) / 256, 256, 0, s>>>(a.xm, a.m, P.L.dir_shift, P.L.x_entries, a.xdir);
   ++*launches;
   return cudaGetLastError();
+}
+
+cudaError_t launch_reencode_planned(const ReencodePlan& plan, const ReencodeArgs& a, cudaStream_t s,
+                                    uint64_t* launches) {
+  ReencodePlanImpl P;
+  memcpy(&P, plan.storage, sizeof(P));
+  if (a.n_main + a.n_delta == 0) return cudaSuccess;
+  P.fn<<<P.grid, P.warps * 32, P.bytes, s>>>(a, P.L);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reencode(uint32_t b, const ReencodeArgs& a, cudaStream_t s, uint32_t sm_count, uint32_t flags,
+                            uint64_t* launches) {
+  if (a.n_main + a.n_delta == 0) return cudaSuccess;
+  ReencodePlan plan;
+  cudaError_t e = plan_reencode(b, a, sm_count, flags, &plan);
+  if (e == cudaSuccess) e = launch_xdir(plan, a, s, launches);
+  if (e == cudaSuccess) e = launch_reencode_planned(plan, a, s, launches);
+  return e;
 }
 
 }  // namespace dm

@@ -1,0 +1,65 @@
+// Directory of X_M for the Step 2(b) lookup (shared by the Step 1 kernel,
+// which builds it after the merge, and by the standalone re-encode path).
+//
+// X_M[i] = i + c[i], where c[i] counts the delta-only values of U' that sort
+// below U_M[i]: a step function of the main code with one step per new value
+// (|U'| - |U_M| steps in all).  The directory cuts the main codes into
+// buckets of 2^s (s <= 10) and keeps, per bucket, c at the bucket's start
+// (base, 20 bits) and the offset thr of the bucket's single step, if it has
+// exactly one, as
+//   entry = (2048 - thr) << 20 | base.
+// For a code i with offset lo = i mod 2^s in its bucket, entry + (lo << 20)
+// carries into bit 31 exactly when lo >= thr, so
+//   X_M[i] = i + (y & 0xFFFFF) + (y >> 31),  y = entry + (lo << 20).
+// A bucket without steps stores thr = 2047 (never reached); a bucket with
+// two or more steps, or whose base needs more than 20 bits, stores the
+// marker thr = 2046 and its codes read X_M itself.
+#pragma once
+
+#include <stdint.h>
+
+namespace dm {
+
+constexpr uint32_t DIR_NONE = 2047, DIR_MANY = 2046;
+constexpr uint32_t DIR_MANY_TOP = 2048 - DIR_MANY;   // top 12 bits of a marked entry
+constexpr uint32_t RE_DIR_MAX = 16384;               // entries (64 KiB of shared memory)
+constexpr uint32_t RE_DIR_SHIFT_MAX = 10;
+
+// Entry of bucket b.  Coherent: X_M was written earlier in the same kernel,
+// so it is read through L2 (ld.global.cg), never from a stale L1 line.
+template <bool Coherent>
+__device__ __forceinline__ uint32_t xdir_entry(const uint32_t* __restrict__ xm, uint32_t m, uint32_t s,
+                                               uint32_t b) {
+  auto ld = [&](uint32_t i) { return Coherent ? __ldcg(xm + i) : __ldg(xm + i); };
+  const uint32_t lo = b << s;
+  const uint32_t hi = min(((b + 1) << s), m) - 1;
+  const uint32_t base = lo == 0 ? 0u : ld(lo - 1) - (lo - 1);
+  const uint32_t cnt = (ld(hi) - hi) - base;
+  uint32_t thr;
+  if (cnt == 0) {
+    thr = DIR_NONE;
+  } else if (cnt == 1) {
+    // first code of the bucket past the step: c[i] > base
+    uint32_t l = lo, h = hi;
+    while (l < h) {
+      uint32_t mid = (l + h) >> 1;
+      if (ld(mid) - mid > base) h = mid;
+      else l = mid + 1;
+    }
+    thr = l - lo;
+  } else {
+    thr = DIR_MANY;
+  }
+  if (base >= (1u << 20)) thr = DIR_MANY;
+  return ((2048u - thr) << 20) | (thr == DIR_MANY ? 0u : base);
+}
+
+// Bucket shift and entry count of the directory for m main codes.
+__host__ __device__ inline void xdir_shape(uint64_t m, uint32_t* shift, uint32_t* entries) {
+  uint32_t sh = 0;
+  while (((m + (1ull << sh) - 1) >> sh) > RE_DIR_MAX) ++sh;
+  *shift = sh;
+  *entries = (uint32_t)((m + (1ull << sh) - 1) >> sh);
+}
+
+}  // namespace dm

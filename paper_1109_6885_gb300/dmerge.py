@@ -33,7 +33,7 @@ EXPORTS = [
     "dm_max_bits", "dm_scratch_bytes", "dm_merge_column", "dm_merge_table",
     "dm_table_scratch_bytes", "dm_merge_column_host", "dm_host_scratch_bytes", "dm_sort_delta",
     "dm_merge_dicts", "dm_reencode", "dm_sync_status", "dm_last_timing", "dm_timing_sum",
-    "dm_launch_count", "dm_merge_dicts_noalloc",
+    "dm_launch_count", "dm_merge_dicts_noalloc", "dm_set_tuning", "dm_get_tuning",
     "dm_status_str",
 ]
 
@@ -57,6 +57,15 @@ class ColumnIn(ctypes.Structure):
         ("delta_dict_len", ctypes.c_uint64),
         ("delta_codes", ctypes.c_void_p),
         ("delta_rows", ctypes.c_uint64),
+    ]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("reencode_warps", ctypes.c_uint32),
+        ("reencode_stages", ctypes.c_uint32),
+        ("reencode_obufs", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 5),
     ]
 
 
@@ -117,6 +126,8 @@ def _load():
             "dm_timing_sum": ([vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(u32)], i32),
             "dm_launch_count": ([vp], u64),
             "dm_status_str": ([i32], ctypes.c_char_p),
+            "dm_set_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
+            "dm_get_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
             "dm_merge_dicts_noalloc": ([u32, vp, u64, vp, vp, u64, vp, vp, vp, vp, vp, vp, vp],
                                        i32),
         }
@@ -207,18 +218,31 @@ class Context:
     def launches(self) -> int:
         return int(_load().dm_launch_count(self.handle))
 
+    def set_tuning(self, **kw):
+        """Launch parameters (reencode_warps, reencode_stages, reencode_obufs; 0 = default)."""
+        t = self.get_tuning()
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _check(_load().dm_set_tuning(self.handle, ctypes.byref(t)), "dm_set_tuning")
+
+    def get_tuning(self) -> Tuning:
+        t = Tuning()
+        _check(_load().dm_get_tuning(self.handle, ctypes.byref(t)), "dm_get_tuning")
+        return t
+
     def sync_status(self, stream=None) -> int:
         return int(_load().dm_sync_status(self.handle, _stream(stream)))
 
     def last_timing(self):
-        """ms of Step 1(a), 1(b)+2(a), 2(b) and the whole last timed merge."""
-        ms = (ctypes.c_float * 4)()
+        """ms of Step 1(a), 1(b)+2(a), the X_M directory, the Step 2(b) kernel and the
+        whole last timed merge."""
+        ms = (ctypes.c_float * 5)()
         _check(_load().dm_last_timing(self.handle, ms), "dm_last_timing")
         return list(ms)
 
     def timing_sum(self):
         """(summed ms per step as in last_timing, number of timed calls); resets."""
-        ms = (ctypes.c_float * 4)()
+        ms = (ctypes.c_float * 5)()
         n = ctypes.c_uint32(0)
         _check(_load().dm_timing_sum(self.handle, ms, ctypes.byref(n)), "dm_timing_sum")
         return list(ms), int(n.value)

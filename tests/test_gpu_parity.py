@@ -350,3 +350,97 @@ def test_merge_table_parity(ctx):
         assert np.array_equal(new_dict, ref.new_dict)
         assert np.array_equal(packed, ref.new_packed)
         assert np.array_equal(xm, ref.x_main) and np.array_equal(xd, ref.x_delta)
+
+
+# ------------------------------------------------------------------ X_M directory
+
+def _steps_table(m, k, rng, clustered=False):
+    """A valid X_M: i + (number of new values inserted at or before main code i)."""
+    if clustered:       # several new values at the same insertion points
+        pts = np.repeat(rng.integers(0, m + 1, max(k // 4, 1)), 4)[:k]
+    else:
+        pts = rng.integers(0, m + 1, k)
+    pts = np.sort(pts)
+    c = np.searchsorted(pts, np.arange(m), side="right")
+    return (np.arange(m) + c).astype(np.uint32), m + k
+
+
+@pytest.mark.parametrize("m,k,clustered", [(20_000, 0, False), (20_000, 150, False),
+                                           (20_000, 20_000, False), (300_000, 3_000, True),
+                                           (1_000_000, 3_000, False), (1_000_000, 300_000, False),
+                                           (5_000_000, 40_000, False)])
+def test_reencode_directory_mode(ctx, m, k, clustered):
+    """X_M looked up through the shared-memory directory (forced) vs the oracle."""
+    import torch
+    rng = np.random.default_rng(m + k)
+    xm, u = _steps_table(m, k, rng, clustered)
+    b, bo = synth.bits_for(m), synth.bits_for(u)
+    n_main, n_delta, d = 1_500_007, 999, 31
+    mc = rng.integers(0, m, n_main).astype(np.uint32)
+    dc = rng.integers(0, d, n_delta).astype(np.uint32)
+    xd = rng.integers(0, u, d).astype(np.uint32)
+    main = synth.pack(mc, b)
+    want = oracle.reencode(main, b, n_main, dc, xm, xd, bo)
+    out = torch.full((dm.dm_packed_bytes(n_main + n_delta, bo) // 4,), -1, dtype=torch.int32,
+                     device="cuda")
+    bits = torch.tensor([bo], dtype=torch.int32, device="cuda")
+    for flags in (dm.DM_FLAG_X_SMEM, dm.DM_FLAG_X_GLOBAL):
+        out.fill_(-1)
+        dm.dm_reencode(ctx, dm.to_device(main), b, n_main, dm.to_device(dc), n_delta,
+                       dm.to_device(xm), m, dm.to_device(xd), d, bits, bo, out, None, flags)
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == dm.DM_OK
+        assert np.array_equal(dm.to_host(out, np.uint32), want), flags
+
+
+@pytest.mark.parametrize("m,n_delta,f_new,pool", [(50_000, 20_000, 0.3, None),
+                                                   (400_000, 100_000, 0.5, 0),
+                                                   (2_000_000, 50_000, 0.3, None)])
+def test_merge_column_directory_mode(ctx, m, n_delta, f_new, pool):
+    spec = synth.ColumnSpec(n_main=3_000_001, m=m, w=8, n_delta=n_delta, f_new=f_new, pool=pool,
+                            dist="zipf", zipf_s=1.0, seed=m ^ n_delta)
+    col = synth.make_column(spec)
+    ref = assert_parity(ctx, col, dm.DM_FLAG_X_SMEM)
+    assert_parity(ctx, col, 0, ref)
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+@pytest.mark.parametrize("w", [8, 16])
+def test_full_size_single_column(ctx, w):
+    """100,000,000 main rows over 1,000,000 values (1% unique), Zipf(1.0) codes at 20
+    bits, 1,000,000 delta rows with 30% new values: every output byte vs the oracle."""
+    spec = synth.ColumnSpec(n_main=100_000_000, m=1_000_000, w=w, n_delta=1_000_000, f_new=0.3,
+                            dist="zipf", zipf_s=1.0, seed=synth.column_seed(2, 0))
+    col = synth.make_column(spec)
+    ref = assert_parity(ctx, col)
+    assert col.main_bits == 20 and ref.new_bits == 20
+
+
+def test_full_size_literal_new_fraction(ctx):
+    """As above with every fresh delta row a distinct new value (300,000 new: 20 -> 21 bits)."""
+    spec = synth.ColumnSpec(n_main=100_000_000, m=1_000_000, w=8, n_delta=1_000_000, f_new=0.3,
+                            pool=0, dist="zipf", zipf_s=1.0, seed=synth.column_seed(2, 1))
+    col = synth.make_column(spec)
+    ref = assert_parity(ctx, col)
+    assert ref.new_bits == 21
+
+
+@pytest.mark.parametrize("warps,stages,obufs", [(4, 2, 1), (8, 4, 2), (12, 3, 2), (16, 2, 1),
+                                                (16, 4, 1), (1, 2, 1)])
+def test_tuning_changes_nothing(warps, stages, obufs):
+    """Launch parameters split the work differently; the bytes stay the same."""
+    from paper_1109_6885_gb300 import build
+    build.build()
+    c = dm.Context(0, 64 << 20)
+    c.set_tuning(reencode_warps=warps, reencode_stages=stages, reencode_obufs=obufs)
+    spec = synth.ColumnSpec(n_main=2_100_003, m=300_000, w=8, n_delta=30_000, f_new=0.3,
+                            dist="zipf", seed=warps * 100 + stages * 10 + obufs)
+    col = synth.make_column(spec)
+    ref = assert_parity(c, col)
+    for flags in (dm.DM_FLAG_X_GLOBAL, dm.DM_FLAG_GENERIC_REENCODE):
+        assert_parity(c, col, flags, ref)
+    small = synth.make_column(synth.ColumnSpec(n_main=1_500_000, m=3000, w=4, n_delta=999,
+                                               seed=warps))
+    assert_parity(c, small, dm.DM_FLAG_X_SMEM)
+    c.close()
