@@ -49,6 +49,13 @@ WORKLOADS = {
     "column-1M-u64-delta10k": dict(n_main=1_000_000, m=100_000, w=8, n_delta=10_000, f_new=0.5,
                                    dist="uniform", pool=0),
 }
+# tables: columns sharing the row counts; per column the dictionary size is
+# log-uniform in [2, max_m], the value width drawn from {4, 8, 16} bytes,
+# codes Zipf(0.8), the delta's new-value fraction uniform in [0, 0.5]
+TABLES = {
+    "table-64x8M-mixed": dict(ncols=64, n_main=8_000_000, n_delta=80_000, max_m=8_000_000),
+    "table-300x50M-mixed": dict(ncols=300, n_main=50_000_000, n_delta=500_000, max_m=50_000_000),
+}
 DEFAULT_WORKLOAD = "column-100M-u64-zipf1-delta1M"
 L2_BYTES = 129 * 2**20
 
@@ -59,7 +66,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(TABLES))
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -363,10 +370,114 @@ def run_e2e(dm, ctx, col, m, d, w, u, b_new, args, world, barrier):
             "path": "dm_merge_column_host: pinned host inputs -> device, merge, results -> host"}
 
 
+def make_table(name: str, rank: int):
+    t = TABLES[name]
+    rng = np.random.default_rng(0x11096885 + rank)
+    cols = []
+    for j in range(t["ncols"]):
+        m = int(np.exp(rng.uniform(np.log(2), np.log(t["max_m"]))))
+        w = int(rng.choice([4, 8, 16]))
+        spec = synth.ColumnSpec(n_main=t["n_main"], m=m, w=w, n_delta=t["n_delta"],
+                                f_new=float(rng.uniform(0, 0.5)), dist="zipf", zipf_s=0.8,
+                                seed=synth.column_seed(4 + 1000 * rank, j))
+        cols.append(synth.make_column(spec))
+    return cols
+
+
+def run_table(args):
+    """Table merges: one batched graph launch vs per-column plain launches."""
+    import torch
+
+    from paper_1109_6885_gb300 import build
+    from paper_1109_6885_gb300 import dmerge as dm
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    dm.load()
+    cols = make_table(args.workload, rank)
+    ctx = dm.Context(local)
+    dcols = [dm.DeviceColumn.from_numpy(c.w, c.main_dict, c.main_packed, c.main_bits, c.n_main,
+                                        c.delta_dict, c.delta_codes) for c in cols]
+    res = [dm.alloc_result(d, with_x=False) for d in dcols]
+    cins = [d.cin() for d in dcols]
+    couts = [r.cout() for r in res]
+    ctx.reserve(max(dm.dm_table_scratch_bytes(cins, 0), dm.dm_table_scratch_bytes(cins, dm.DM_FLAG_SERIAL)))
+    stream = torch.cuda.current_stream()
+    tuples = sum(c.n_main + c.n_delta for c in cols)
+
+    def timed(flags):
+        for _ in range(max(args.warmup, 3)):
+            dm.dm_merge_table(ctx, cins, couts, stream, flags)
+        torch.cuda.synchronize()
+        if ctx.sync_status() != dm.DM_OK:
+            raise RuntimeError("device status after warm-up")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for k in range(args.steps):
+            dm.dm_merge_table(ctx, cins, couts, stream, flags)
+            ev[k + 1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        per = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps))
+        total = ev[0].elapsed_time(ev[args.steps])
+        if world > 1:
+            t = torch.tensor([total], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        return total, per
+
+    launches0 = ctx.launches
+    sampler = ClockSampler(local, not args.no_clocks)
+    t_batched, per_b = timed(0)
+    clocks = sampler.stop()
+    launches = (ctx.launches - launches0) // (args.steps + max(args.warmup, 3))
+    t_serial, per_s = timed(dm.DM_FLAG_SERIAL)
+    step2 = 0
+    for c, r in zip(cols, res):
+        u, b = r.u_bits()
+        step2 += traffic.step2_bytes(c.main_bits, b, c.n_main, c.n_delta, c.main_dict.shape[0],
+                                     c.delta_dict.shape[0])
+    pct = lambda v, q: v[min(len(v) - 1, int(q * len(v)))]
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        line = {
+            "metric": "merged tuple-columns/s per table", "value": world * tuples * args.steps / (t_batched / 1e3),
+            "unit": "tuple-columns/s", "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": t_batched / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "mixed u32/u64/u128", "data": "synthetic",
+            "config": {"workload": args.workload, **TABLES[args.workload],
+                       "form": "one CUDA-graph launch per table (4 branches)",
+                       "l2": "inputs larger than L2"},
+            "latency_ms": {"p50": pct(per_b, 0.5), "p99": pct(per_b, 0.99)},
+            "serial": {"value": world * tuples * args.steps / (t_serial / 1e3), "ms_per_step": t_serial / args.steps,
+                       "latency_ms": {"p50": pct(per_s, 0.5), "p99": pct(per_s, 0.99)},
+                       "form": "per-column plain launches, one stream"},
+            "speedup_vs_serial": t_serial / t_batched,
+            "step2_bytes_per_table": step2,
+            "table_hbm_gbs_effective": step2 / (t_batched / args.steps / 1e3) / 1e9, "hbm_peak_gbs": peak,
+            "gpu_launches": launches, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in TABLES:
+        run_table(args)
     else:
         run_gpu(args)
 

@@ -78,6 +78,7 @@ typedef enum {
 #define DM_FLAG_X_SMEM 0x2u            /* look X_M up in shared memory at any size (table or directory) */
 #define DM_FLAG_X_GLOBAL 0x4u          /* never stage X_M in shared memory */
 #define DM_FLAG_TIMING 0x8u            /* record per-step CUDA events (dm_last_timing) */
+#define DM_FLAG_SERIAL 0x10u           /* dm_merge_table: one column after another, plain launches */
 
 typedef struct dm_ctx dm_ctx;
 
@@ -132,7 +133,15 @@ dm_status dm_merge_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_o
 
 /* Merge ncols columns of one table (Section 6.2.1 scheme (i): columns are
  * independent tasks).  Same contract as dm_merge_column per column; the
- * arena must hold dm_table_scratch_bytes. */
+ * arena must hold dm_table_scratch_bytes (flags as passed here).
+ *
+ * By default the table runs as ONE CUDA-graph launch: the columns' kernels
+ * are recorded once, round-robin over four branches, so that the latency-
+ * bound Step 1 of some columns overlaps the bandwidth-bound Step 2(b) of
+ * others, and replayed on later calls with the same argument bytes (the
+ * same buffers; up to eight argument sets are kept per context).  With
+ * DM_FLAG_SERIAL the columns run one after another with plain launches.
+ * Not for use inside a caller's own stream capture. */
 dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols,
                          const dm_column_out* out, void* stream, uint32_t flags);
 size_t dm_table_scratch_bytes(const dm_column_in* in, uint32_t ncols, uint32_t flags);
@@ -244,6 +253,10 @@ uint64_t dm_launch_count(const dm_ctx* ctx);
 
 /* Name of a status code. */
 const char* dm_status_str(dm_status s);
+
+/* Text of the last CUDA runtime error a call on this context met (the
+ * detail behind DM_ECUDA). */
+const char* dm_last_error(const dm_ctx* ctx);
 
 #ifdef __cplusplus
 }

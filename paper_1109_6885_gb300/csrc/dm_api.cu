@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <new>
+#include <string>
+#include <vector>
 
 #include "../../include/dmerge.h"
 #include "dm_common.cuh"
@@ -28,6 +30,21 @@ struct dm_ctx {
   uint32_t ring_n = 0;
   cudaEvent_t* last_ev = nullptr;   // quadruple of the last timed call
   dm_tuning tuning{};
+  // batched table merges: side streams, fork/join events, graph cache
+  static constexpr uint32_t kTableStreams = 4;
+  cudaStream_t side[kTableStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kTableStreams] = {};
+  struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;   // kernels in the graph
+    uint64_t last_use = 0;
+  };
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  cudaStream_t capture = nullptr;   // graphs are recorded here, never on a caller's stream
+  cudaError_t last_error = cudaSuccess;
   uint64_t launches = 0;
 };
 
@@ -137,7 +154,8 @@ dm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DM_OK : DM_ECUD
 // and the X_M directory (one kernel: both at its end), before the Step 2(b)
 // kernel and at the end (nullptr: no timing).
 dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* base,
-                     cudaStream_t s, uint32_t flags, cudaEvent_t* ev) {
+                     cudaStream_t s, uint32_t flags, cudaEvent_t* ev, const dm::ReencodePlan* pre_plan = nullptr,
+                     uint32_t grid_cap = 0) {
   const bool timing = ev != nullptr;
   ColumnScratch cs;
   carve_column(base, in, out, &cs);
@@ -165,7 +183,8 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
   ra.tune_stages = ctx->tuning.reencode_stages;
   ra.tune_obufs = ctx->tuning.reencode_obufs;
   dm::ReencodePlan plan{};
-  if (n_out && dm::plan_reencode(in->main_bits, ra, ctx->sm_count, flags, &plan) != cudaSuccess) return DM_ECUDA;
+  if (pre_plan) plan = *pre_plan;
+  else if (n_out && dm::plan_reencode(in->main_bits, ra, ctx->sm_count, flags, &plan) != cudaSuccess) return DM_ECUDA;
 
   cudaError_t e = cudaMemsetAsync(cs.zero, 0, cs.zero_bytes, s);
   if (e != cudaSuccess) return DM_ECUDA;
@@ -180,7 +199,9 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
     a.dir_shift = plan.dir_shift;
     a.dir_entries = plan.dir_entries;
     a.status = ctx->status;
+    a.grid_cap = grid_cap;
     e = dm::launch_step1(w, a, s, ctx->sm_count, &ctx->launches);
+    if (e != cudaSuccess) ctx->last_error = e;
   } else {
     e = cudaMemsetAsync(out->d_new_dict_len, 0, sizeof(uint64_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(out->d_new_bits, 0, sizeof(uint32_t), s);
@@ -193,7 +214,10 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
   }
   if (n_out) {
     e = dm::launch_reencode_planned(plan, ra, s, &ctx->launches);
-    if (e != cudaSuccess) return DM_ECUDA;
+    if (e != cudaSuccess) {
+      ctx->last_error = e;
+      return DM_ECUDA;
+    }
   }
   if (timing) cudaEventRecord(ev[4], s);
   return DM_OK;
@@ -204,6 +228,10 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 }  // namespace
 
 extern "C" {
+
+const char* dm_last_error(const dm_ctx* ctx) {
+  return ctx ? cudaGetErrorString(ctx->last_error) : "no context";
+}
 
 const char* dm_status_str(dm_status s) {
   switch (s) {
@@ -234,8 +262,9 @@ size_t dm_scratch_bytes(const dm_column_in* in, uint32_t) {
 
 size_t dm_table_scratch_bytes(const dm_column_in* in, uint32_t ncols, uint32_t flags) {
   size_t mx = 0;
-  for (uint32_t c = 0; c < ncols; ++c) mx = std::max(mx, dm_scratch_bytes(&in[c], flags));
-  return mx;
+  for (uint32_t c = 0; c < ncols; ++c) mx = std::max(mx, align_up(dm_scratch_bytes(&in[c], flags)));
+  if (flags & DM_FLAG_SERIAL) return mx;
+  return mx * std::min<uint32_t>(ncols, dm_ctx::kTableStreams);
 }
 
 dm_status dm_create(dm_ctx** out, int device, size_t arena_bytes) {
@@ -268,6 +297,15 @@ dm_status dm_create(dm_ctx** out, int device, size_t arena_bytes) {
       return DM_ECUDA;
     }
   }
+  bool ok = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) == cudaSuccess;
+  for (uint32_t i = 0; ok && i < dm_ctx::kTableStreams; ++i)
+    ok = cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ctx->join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    dm_destroy(ctx);
+    return DM_ECUDA;
+  }
   if (arena_bytes) {
     dm_status st = dm_reserve(ctx, arena_bytes);
     if (st != DM_OK) {
@@ -289,6 +327,14 @@ void dm_destroy(dm_ctx* ctx) {
   if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
   for (auto e : ctx->ev)
     if (e) cudaEventDestroy(e);
+  for (auto& g : ctx->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (uint32_t i = 0; i < dm_ctx::kTableStreams; ++i) {
+    if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+    if (ctx->join[i]) cudaEventDestroy(ctx->join[i]);
+  }
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
   if (ctx->ring) {
     for (uint32_t i = 0; i < 5 * dm_ctx::kRing; ++i)
       if (ctx->ring[i]) cudaEventDestroy(ctx->ring[i]);
@@ -344,6 +390,32 @@ dm_status dm_merge_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_o
   return st;
 }
 
+namespace {
+
+// Record the batched schedule of a table on `s` (already capturing): columns
+// round-robin over the side streams, each stream with its own scratch.
+dm_status record_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, const dm_column_out* out,
+                       cudaStream_t s, uint32_t flags, const std::vector<dm::ReencodePlan>& plans, uint32_t S,
+                       size_t region) {
+  if (cudaEventRecord(ctx->fork, s) != cudaSuccess) return DM_ECUDA;
+  for (uint32_t i = 0; i < S; ++i)
+    if (cudaStreamWaitEvent(ctx->side[i], ctx->fork, 0) != cudaSuccess) return DM_ECUDA;
+  for (uint32_t c = 0; c < ncols; ++c) {
+    const uint32_t i = c % S;
+    const uint32_t cap = dm::step1_capacity(in[c].value_bytes, ctx->sm_count) / S;
+    void* base = static_cast<char*>(ctx->arena) + (size_t)i * region;
+    dm_status st = run_column(ctx, &in[c], &out[c], base, ctx->side[i], flags, nullptr, &plans[c], cap ? cap : 1);
+    if (st != DM_OK) return st;
+  }
+  for (uint32_t i = 0; i < S; ++i) {
+    if (cudaEventRecord(ctx->join[i], ctx->side[i]) != cudaSuccess) return DM_ECUDA;
+    if (cudaStreamWaitEvent(s, ctx->join[i], 0) != cudaSuccess) return DM_ECUDA;
+  }
+  return DM_OK;
+}
+
+}  // namespace
+
 dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, const dm_column_out* out,
                          void* stream, uint32_t flags) {
   if (!ctx || (ncols && (!in || !out))) return DM_EINVAL;
@@ -353,13 +425,98 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
   }
   if (dm_table_scratch_bytes(in, ncols, flags) > ctx->arena_bytes) return DM_ENOMEM;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
-  // columns are independent tasks; on one stream they reuse one scratch region
-  for (uint32_t c = 0; c < ncols; ++c) {
-    dm_status st = run_column(ctx, &in[c], &out[c], ctx->arena, as_stream(stream), flags, nullptr);
-    if (st != DM_OK) return st;
-  }
+  cudaStream_t s = as_stream(stream);
   ctx->timing_valid = false;
-  return DM_OK;
+  if (ncols == 0) return DM_OK;
+  if (flags & DM_FLAG_SERIAL) {
+    // columns one after another on one stream, reusing one scratch region
+    for (uint32_t c = 0; c < ncols; ++c) {
+      dm_status st = run_column(ctx, &in[c], &out[c], ctx->arena, s, flags, nullptr);
+      if (st != DM_OK) return st;
+    }
+    return DM_OK;
+  }
+
+  // batched: one CUDA graph holds every column's kernels on kTableStreams
+  // branches; it is recorded once per distinct argument set and replayed
+  const uint32_t S = std::min<uint32_t>(ncols, dm_ctx::kTableStreams);
+  size_t region = 0;
+  for (uint32_t c = 0; c < ncols; ++c) region = std::max(region, align_up(dm_scratch_bytes(&in[c], flags)));
+  std::string key;
+  key.reserve(64 + ncols * (sizeof(dm_column_in) + sizeof(dm_column_out)));
+  auto put = [&key](const void* p, size_t n) { key.append(static_cast<const char*>(p), n); };
+  put(&ncols, sizeof(ncols));
+  put(&flags, sizeof(flags));
+  put(&ctx->arena, sizeof(ctx->arena));
+  put(&ctx->tuning, sizeof(ctx->tuning));
+  for (uint32_t c = 0; c < ncols; ++c) {
+    put(&in[c], sizeof(dm_column_in));
+    put(&out[c], sizeof(dm_column_out));
+  }
+  ++ctx->graph_clock;
+  for (auto& g : ctx->graphs) {
+    if (g.key == key) {
+      g.last_use = ctx->graph_clock;
+      ctx->launches += g.launches;
+      const cudaError_t le = cudaGraphLaunch(g.exec, s);
+      if (le != cudaSuccess) ctx->last_error = le;
+      return le == cudaSuccess ? DM_OK : DM_ECUDA;
+    }
+  }
+  // plan every launch before recording (attribute and occupancy queries
+  // stay out of the capture)
+  if (dm::step1_prepare() != cudaSuccess) return DM_ECUDA;
+  std::vector<dm::ReencodePlan> plans(ncols);
+  for (uint32_t c = 0; c < ncols; ++c) {
+    if (in[c].main_rows + in[c].delta_rows == 0) continue;
+    dm::ReencodeArgs ra{};
+    ra.n_main = in[c].main_rows;
+    ra.n_delta = in[c].delta_rows;
+    ra.m = (uint32_t)std::min<uint64_t>(in[c].main_dict_len, 0xFFFFFFFFu);
+    ra.max_bits = bits_for(in[c].main_dict_len + in[c].delta_dict_len);
+    ra.xdir = reinterpret_cast<uint32_t*>(16);   // a directory will exist
+    ra.tune_warps = ctx->tuning.reencode_warps;
+    ra.tune_stages = ctx->tuning.reencode_stages;
+    ra.tune_obufs = ctx->tuning.reencode_obufs;
+    if (dm::plan_reencode(in[c].main_bits, ra, ctx->sm_count, flags, &plans[c]) != cudaSuccess) return DM_ECUDA;
+  }
+  const uint64_t launches0 = ctx->launches;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    ctx->last_error = e;
+    return DM_ECUDA;
+  }
+  dm_status st = record_table(ctx, in, ncols, out, ctx->capture, flags, plans, S, region);
+  e = cudaStreamEndCapture(ctx->capture, &graph);
+  if (st != DM_OK || e != cudaSuccess) {
+    if (e != cudaSuccess) ctx->last_error = e;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return st != DM_OK ? st : DM_ECUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    ctx->last_error = e;
+    return DM_ECUDA;
+  }
+  dm_ctx::GraphEntry ent;
+  ent.key = std::move(key);
+  ent.exec = exec;
+  ent.launches = ctx->launches - launches0;
+  ent.last_use = ctx->graph_clock;
+  if (ctx->graphs.size() >= 8) {
+    auto lru = std::min_element(ctx->graphs.begin(), ctx->graphs.end(),
+                                [](const auto& a, const auto& b) { return a.last_use < b.last_use; });
+    cudaGraphExecDestroy(lru->exec);
+    ctx->graphs.erase(lru);
+  }
+  ctx->graphs.push_back(std::move(ent));
+  e = cudaGraphLaunch(exec, s);
+  if (e != cudaSuccess) ctx->last_error = e;
+  return e == cudaSuccess ? DM_OK : DM_ECUDA;
 }
 
 size_t dm_host_scratch_bytes(const dm_column_in* in, uint32_t flags) {

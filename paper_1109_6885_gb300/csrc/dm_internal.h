@@ -44,7 +44,13 @@ struct Step1Args {
   uint32_t phases;           // S1_SORT | S1_MERGE | S1_DIR
   uint32_t* barriers;        // [S1_BARRIERS] (zeroed)
   uint32_t* status;
+  uint32_t grid_cap;         // 0: whole device; else at most this many blocks
 };
+
+// Set the Step 1 kernels' launch attributes (outside any stream capture).
+cudaError_t step1_prepare();
+// Blocks of one Step 1 launch that can be resident on the device at once.
+uint32_t step1_capacity(uint32_t w, uint32_t sm_count);
 
 uint32_t sort_tiles(uint64_t d);
 uint32_t merge_tiles(uint64_t n);

@@ -684,20 +684,31 @@ Launch& launch_state() {
 }
 
 template <int W>
+cudaError_t prepare_w() {
+  const int wi = W == 4 ? 0 : (W == 8 ? 1 : 2);
+  Launch& L = launch_state();
+  std::lock_guard<std::mutex> g(L.mu);
+  if (L.ready[wi]) return cudaSuccess;
+  const size_t smem = step1_smem_bytes<W>();
+  cudaError_t e = cudaFuncSetAttribute(step1_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.per_sm[wi], step1_kernel<W>, S1_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  L.ready[wi] = true;
+  return cudaSuccess;
+}
+
+
+template <int W>
 cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint64_t* launches) {
   const int wi = W == 4 ? 0 : (W == 8 ? 1 : 2);
   const size_t smem = step1_smem_bytes<W>();
+  cudaError_t pe = prepare_w<W>();
+  if (pe != cudaSuccess) return pe;
   Launch& L = launch_state();
   int per_sm;
   {
     std::lock_guard<std::mutex> g(L.mu);
-    if (!L.ready[wi]) {
-      cudaError_t e = cudaFuncSetAttribute(step1_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.per_sm[wi], step1_kernel<W>, S1_THREADS, smem);
-      if (e != cudaSuccess) return e;
-      L.ready[wi] = true;
-    }
     per_sm = L.per_sm[wi];
   }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
@@ -707,7 +718,8 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
   if ((a.phases & S1_SORT) && a.d > BK_SINGLE) want = std::max<uint64_t>(want, std::max<uint64_t>(a.sort_tiles, 256));
   if (a.phases & S1_MERGE) want = std::max<uint64_t>(want, a.merge_tiles);
   if (a.phases & S1_DIR) want = std::max<uint64_t>(want, (a.dir_entries + S1_THREADS - 1) / S1_THREADS);
-  const uint64_t cap = (uint64_t)per_sm * sm_count;
+  uint64_t cap = (uint64_t)per_sm * sm_count;
+  if (a.grid_cap && a.grid_cap < cap) cap = a.grid_cap;
   const uint32_t grid = (uint32_t)std::min(want, cap);
   a.hist_blocks = (uint32_t)std::min<uint64_t>(grid, std::max<uint64_t>(1, (a.d + 4095) / 4096));
 
@@ -727,6 +739,21 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
 }
 
 }  // namespace
+
+cudaError_t step1_prepare() {
+  cudaError_t e = prepare_w<4>();
+  if (e == cudaSuccess) e = prepare_w<8>();
+  if (e == cudaSuccess) e = prepare_w<16>();
+  return e;
+}
+
+uint32_t step1_capacity(uint32_t w, uint32_t sm_count) {
+  if (step1_prepare() != cudaSuccess) return 0;
+  Launch& L = launch_state();
+  std::lock_guard<std::mutex> g(L.mu);
+  const int wi = w == 4 ? 0 : (w == 8 ? 1 : 2);
+  return (uint32_t)L.per_sm[wi] * sm_count;
+}
 
 uint32_t sort_tiles(uint64_t d) { return (uint32_t)((d + RS_TILE - 1) / RS_TILE); }
 uint32_t merge_tiles(uint64_t n) { return (uint32_t)((n + MG_TILE - 1) / MG_TILE); }

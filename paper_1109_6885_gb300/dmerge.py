@@ -27,13 +27,14 @@ DM_FLAG_GENERIC_REENCODE = 0x1
 DM_FLAG_X_SMEM = 0x2
 DM_FLAG_X_GLOBAL = 0x4
 DM_FLAG_TIMING = 0x8
+DM_FLAG_SERIAL = 0x10
 
 EXPORTS = [
     "dm_create", "dm_destroy", "dm_reserve", "dm_arena_bytes", "dm_packed_bytes", "dm_bits_for",
     "dm_max_bits", "dm_scratch_bytes", "dm_merge_column", "dm_merge_table",
     "dm_table_scratch_bytes", "dm_merge_column_host", "dm_host_scratch_bytes", "dm_sort_delta",
     "dm_merge_dicts", "dm_reencode", "dm_sync_status", "dm_last_timing", "dm_timing_sum",
-    "dm_launch_count", "dm_merge_dicts_noalloc", "dm_set_tuning", "dm_get_tuning",
+    "dm_launch_count", "dm_merge_dicts_noalloc", "dm_set_tuning", "dm_get_tuning", "dm_last_error",
     "dm_status_str",
 ]
 
@@ -127,6 +128,7 @@ def _load():
             "dm_launch_count": ([vp], u64),
             "dm_status_str": ([i32], ctypes.c_char_p),
             "dm_set_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
+            "dm_last_error": ([vp], ctypes.c_char_p),
             "dm_get_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
             "dm_merge_dicts_noalloc": ([u32, vp, u64, vp, vp, u64, vp, vp, vp, vp, vp, vp, vp],
                                        i32),
@@ -139,8 +141,10 @@ def _load():
         return lib
 
 
-def _check(rc: int, what: str):
+def _check(rc: int, what: str, ctx=None):
     if rc != DM_OK:
+        if rc == DM_ECUDA and ctx is not None and ctx.handle:
+            what = f"{what} ({_load().dm_last_error(ctx.handle).decode()})"
         raise DmError(rc, what)
 
 
@@ -250,7 +254,7 @@ class Context:
 
 def dm_merge_column(ctx: Context, cin: ColumnIn, cout: ColumnOut, stream=None, flags: int = 0):
     _check(_load().dm_merge_column(ctx.handle, ctypes.byref(cin), ctypes.byref(cout),
-                                   _stream(stream), flags), "dm_merge_column")
+                                   _stream(stream), flags), "dm_merge_column", ctx)
 
 
 def dm_merge_table(ctx: Context, cins, couts, stream=None, flags: int = 0):
@@ -258,7 +262,7 @@ def dm_merge_table(ctx: Context, cins, couts, stream=None, flags: int = 0):
     ain = (ColumnIn * n)(*cins)
     aout = (ColumnOut * n)(*couts)
     _check(_load().dm_merge_table(ctx.handle, ain, n, aout, _stream(stream), flags),
-           "dm_merge_table")
+           "dm_merge_table", ctx)
 
 
 def dm_merge_column_host(ctx: Context, cin: ColumnIn, cout: ColumnOut, stream=None,

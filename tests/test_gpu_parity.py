@@ -321,28 +321,24 @@ def test_host_buffer_entry_point(ctx):
     assert np.array_equal(xm, ref.x_main) and np.array_equal(xd, ref.x_delta)
 
 
-def test_merge_table_parity(ctx):
-    import torch
-    rng = np.random.default_rng(5)
+def _table(rng, ncols, n_main, n_delta, max_m, config=4):
     cols, dcols, results = [], [], []
-    n_main, n_delta = 200_000, 3_000
-    for j in range(6):
-        m = int(np.exp(rng.uniform(np.log(2), np.log(150_000))))
+    for j in range(ncols):
+        m = int(np.exp(rng.uniform(np.log(2), np.log(max_m))))
         w = int(rng.choice([4, 8, 16]))
         spec = synth.ColumnSpec(n_main=n_main, m=m, w=w, n_delta=n_delta,
                                 f_new=float(rng.uniform(0, 0.5)), dist="zipf", zipf_s=0.8,
-                                seed=synth.column_seed(4, j))
+                                seed=synth.column_seed(config, j))
         col = synth.make_column(spec)
         cols.append(col)
         dc = dm.DeviceColumn.from_numpy(col.w, col.main_dict, col.main_packed, col.main_bits,
                                         col.n_main, col.delta_dict, col.delta_codes)
         dcols.append(dc)
         results.append(dm.alloc_result(dc))
-    cins = [c.cin() for c in dcols]
-    ctx.reserve(dm.dm_table_scratch_bytes(cins))
-    dm.dm_merge_table(ctx, cins, [r.cout() for r in results])
-    torch.cuda.synchronize()
-    assert ctx.sync_status() == dm.DM_OK
+    return cols, dcols, results
+
+
+def _check_table(cols, results):
     for col, res in zip(cols, results):
         ref = oracle.merge_synth_column(col)
         new_dict, xm, xd, packed, b, u = dm.fetch(res, col.w, col.n_main + col.n_delta)
@@ -350,6 +346,47 @@ def test_merge_table_parity(ctx):
         assert np.array_equal(new_dict, ref.new_dict)
         assert np.array_equal(packed, ref.new_packed)
         assert np.array_equal(xm, ref.x_main) and np.array_equal(xd, ref.x_delta)
+
+
+@pytest.mark.parametrize("flags", [0, dm.DM_FLAG_SERIAL])
+def test_merge_table_parity(ctx, flags):
+    """Batched (one graph launch) and serial table merges vs the per-column oracle."""
+    import torch
+    rng = np.random.default_rng(5)
+    cols, dcols, results = _table(rng, 9, 300_007, 3_001, 300_000)
+    cins = [c.cin() for c in dcols]
+    ctx.reserve(dm.dm_table_scratch_bytes(cins, flags))
+    dm.dm_merge_table(ctx, cins, [r.cout() for r in results], flags=flags)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_OK
+    _check_table(cols, results)
+
+
+def test_merge_table_graph_replay_sees_new_data(ctx):
+    """A replayed table graph reads the buffers' current contents."""
+    import torch
+    rng = np.random.default_rng(6)
+    cols, dcols, results = _table(rng, 5, 200_003, 2_000, 100_000)
+    cins = [c.cin() for c in dcols]
+    couts = [r.cout() for r in results]
+    ctx.reserve(dm.dm_table_scratch_bytes(cins))
+    dm.dm_merge_table(ctx, cins, couts)
+    torch.cuda.synchronize()
+    _check_table(cols, results)
+    # same buffers, new codes: rewrite each column's main vector and delta codes in place
+    new_cols = []
+    for j, (col, dc) in enumerate(zip(cols, dcols)):
+        mc = synth.codes(1000 + j, col.main_dict.shape[0], col.n_main)
+        packed = synth.pack(mc, col.main_bits)
+        dcodes = synth.codes(2000 + j, col.delta_dict.shape[0], col.n_delta)
+        dc.main_packed.copy_(dm.to_device(packed))
+        dc.delta_codes.copy_(dm.to_device(dcodes))
+        new_cols.append(synth.Column(col.spec, col.main_dict, mc, col.main_bits, packed,
+                                     col.delta_dict, dcodes))
+    dm.dm_merge_table(ctx, cins, couts)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_OK
+    _check_table(new_cols, results)
 
 
 # ------------------------------------------------------------------ X_M directory
