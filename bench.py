@@ -56,6 +56,14 @@ TABLES = {
     "table-64x8M-mixed": dict(ncols=64, n_main=8_000_000, n_delta=80_000, max_m=8_000_000),
     "table-300x50M-mixed": dict(ncols=300, n_main=50_000_000, n_delta=500_000, max_m=50_000_000),
 }
+# served merges: resident tables of 20-60 columns, main rows log-uniform in
+# [100k, 4M], delta 0.1-10% of main; Poisson arrivals at `rate` requests/s
+SERVES = {
+    "serve-16tables-poisson20": dict(ntables=16, cols=(20, 60), rows=(100_000, 4_000_000), rate=20.0,
+                                     requests=200, slots=4, budget=16 << 30),
+    "serve-16tables-burst": dict(ntables=16, cols=(20, 60), rows=(100_000, 4_000_000), rate=0.0,
+                                 requests=200, slots=4, budget=16 << 30),
+}
 DEFAULT_WORKLOAD = "column-100M-u64-zipf1-delta1M"
 L2_BYTES = 129 * 2**20
 
@@ -66,7 +74,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(TABLES))
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                   choices=sorted(WORKLOADS) + sorted(TABLES) + sorted(SERVES))
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -472,12 +481,94 @@ def run_table(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serve(args):
+    """Served merges: Poisson (or burst) arrivals of table merges, continuous batching."""
+    import torch
+
+    from paper_1109_6885_gb300 import build
+    from paper_1109_6885_gb300 import dmerge as dm
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    dm.load()
+    cfg = SERVES[args.workload]
+    rng = np.random.default_rng(0x5E7E + rank)
+    srv = dm.Server(local, slots=cfg["slots"], scratch_budget=cfg["budget"])
+    keep = []
+    for t in range(cfg["ntables"]):
+        ncols = int(rng.integers(cfg["cols"][0], cfg["cols"][1] + 1))
+        n_main = int(np.exp(rng.uniform(np.log(cfg["rows"][0]), np.log(cfg["rows"][1]))))
+        n_delta = max(1, int(n_main * np.exp(rng.uniform(np.log(0.001), np.log(0.1)))))
+        cins, couts = [], []
+        for j in range(ncols):
+            m = int(np.exp(rng.uniform(np.log(2), np.log(n_main))))
+            spec = synth.ColumnSpec(n_main=n_main, m=m, w=int(rng.choice([4, 8, 16])), n_delta=n_delta,
+                                    f_new=float(rng.uniform(0, 0.5)), dist="zipf", zipf_s=0.8,
+                                    seed=synth.column_seed(5 + 1000 * rank + t, j))
+            c = synth.make_column(spec)
+            d = dm.DeviceColumn.from_numpy(c.w, c.main_dict, c.main_packed, c.main_bits, c.n_main,
+                                           c.delta_dict, c.delta_codes)
+            r = dm.alloc_result(d, with_x=False)
+            keep.append((d, r))
+            cins.append(d.cin())
+            couts.append(r.cout())
+        srv.add_table(t, cins, couts)
+    # warm-up: one merge of every table (records their graphs)
+    for t in range(cfg["ntables"]):
+        srv.submit(t)
+    srv.drain()
+    base = srv.stats()
+    nreq = max(args.steps * 10, cfg["requests"])
+    tabs = rng.integers(0, cfg["ntables"], nreq)
+    gaps = rng.exponential(1.0 / cfg["rate"], nreq) if cfg["rate"] > 0 else np.zeros(nreq)
+    sampler = ClockSampler(local, not args.no_clocks)
+    t0 = time.perf_counter()
+    due = t0
+    for t, g in zip(tabs, gaps):
+        due += g
+        while True:
+            now = time.perf_counter()
+            if now >= due:
+                break
+            time.sleep(min(due - now, 0.002))
+        srv.submit(int(t))
+    srv.drain()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    st = srv.stats()
+    # latency over the timed requests only
+    lat = []
+    for rid in range(base.submitted, st.submitted):
+        info = srv.info(rid)
+        lat.append((info.done_ns - info.submit_ns) / 1e6)
+    lat.sort()
+    tuples = st.tuples - base.tuples
+    if rank == 0:
+        line = {
+            "metric": "served merged tuple-columns/s; p50/p99 merge latency", "value": tuples / wall,
+            "unit": "tuple-columns/s", "n_gpus": world, "steps": nreq, "warmup": cfg["ntables"],
+            "ms_per_step": 1e3 * wall / nreq, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "mixed u32/u64/u128", "data": "synthetic",
+            "config": {"workload": args.workload, **{k: v for k, v in cfg.items()}},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "max": lat[-1]},
+            "requests": nreq, "failed": st.failed - base.failed,
+            "peak_concurrency": st.peak_concurrency, "peak_scratch_bytes": st.peak_scratch_bytes,
+            "scratch_budget": st.scratch_budget, "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    srv.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload in TABLES:
         run_table(args)
+    elif args.workload in SERVES:
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -218,6 +218,72 @@ dm_status dm_merge_dicts_noalloc(uint32_t value_bytes, const void* main_dict, ui
                                  uint64_t* d_u, uint32_t* d_bits, uint32_t* d_status,
                                  void* stream);
 
+/* ---- served merges (continuous batching) ---- */
+
+/* A merge server: registered tables stay resident on the device; merge
+ * requests arriving over time are admitted into `slots` concurrent table
+ * merges whenever a slot is free, the table has no merge in flight, and a
+ * contiguous region of the scratch pool of `scratch_budget` bytes holds the
+ * request's footprint (dm_table_scratch_bytes of its columns).  A host
+ * thread watches completions, commits each table's new version (the
+ * registry's pointer swap of the paper's atomic commit, Section 3), frees
+ * the region and admits the next requests, so work that arrives while
+ * other merges run joins them on the device.  Results land in the output
+ * buffers given at registration; a table serves one merge at a time. */
+typedef struct dm_server dm_server;
+
+typedef struct {
+  uint32_t slots;            /* concurrent table merges, 1..16 */
+  uint64_t scratch_budget;   /* bytes of the scratch pool: the admission budget */
+  uint32_t flags;            /* passed to dm_merge_table (0: one graph launch per table) */
+} dm_server_config;
+
+typedef struct {
+  uint32_t table_id;
+  int32_t status;            /* dm_status of the merge; -1 while not finished */
+  uint64_t submit_ns, admit_ns, done_ns;   /* server clock (steady, from creation) */
+  uint64_t footprint;        /* scratch bytes it held */
+  uint32_t slot;
+} dm_request_info;
+
+typedef struct {
+  uint64_t submitted, completed, failed;
+  uint64_t tuples;           /* N_M + N_D summed over the columns of completed merges */
+  double p50_ms, p99_ms, max_ms, mean_ms;   /* submit -> completion latency */
+  uint64_t first_submit_ns, last_done_ns;
+  uint64_t peak_scratch_bytes;   /* most scratch ever held at once (<= scratch_budget) */
+  uint64_t scratch_budget;
+  uint32_t peak_concurrency;     /* most merges ever running at once */
+} dm_server_stats;
+
+dm_status dm_server_create(dm_server** server, int device, const dm_server_config* cfg);
+/* Stops the scheduler thread (pending requests are dropped) and frees the pool. */
+void dm_server_destroy(dm_server* server);
+/* Register table `table_id`: ncols columns (device pointers, caller-owned,
+ * valid until the server is destroyed).  DM_ENOMEM: its footprint exceeds
+ * the pool. */
+dm_status dm_server_add_table(dm_server* server, uint32_t table_id, const dm_column_in* in, uint32_t ncols,
+                              const dm_column_out* out);
+/* Queue a merge of the table; returns at once. */
+dm_status dm_server_submit(dm_server* server, uint32_t table_id, uint64_t* request_id);
+/* Wait until every submitted request has finished (DM_EBUSY on timeout). */
+dm_status dm_server_drain(dm_server* server, uint64_t timeout_ms);
+dm_status dm_server_request_info(dm_server* server, uint64_t request_id, dm_request_info* info);
+dm_status dm_server_stats_get(dm_server* server, dm_server_stats* stats);
+/* Committed merges of the table so far. */
+uint64_t dm_server_table_version(dm_server* server, uint32_t table_id);
+
+/* The server's admission rules run on a fake clock (no GPU): requests of
+ * table req_table[i] arrive at arrival_ns[i] (non-decreasing); a merge of
+ * table t holds footprint[t] scratch bytes for service_ns[t].  Fills each
+ * request's admission and completion times and slot, and the peaks of
+ * scratch in use and of merges running at once.  For testing and
+ * capacity planning. */
+dm_status dm_sched_simulate(uint64_t pool_bytes, uint32_t slots, uint32_t ntables, const uint64_t* footprint,
+                            const uint64_t* service_ns, uint64_t nreq, const uint32_t* req_table,
+                            const uint64_t* arrival_ns, uint64_t* admit_ns, uint64_t* done_ns,
+                            uint32_t* slot_out, uint64_t* peak_bytes, uint32_t* peak_running);
+
 /* ---- status, timing, introspection ---- */
 
 /* Wait for `stream`, read and clear the context's device status word:

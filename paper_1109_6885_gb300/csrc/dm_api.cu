@@ -13,40 +13,7 @@
 #include "dm_common.cuh"
 #include "dm_internal.h"
 
-struct dm_ctx {
-  int device = 0;
-  uint32_t sm_count = 0;
-  void* arena = nullptr;
-  size_t arena_bytes = 0;
-  uint32_t* status = nullptr;      // device status word
-  uint32_t* host_status = nullptr; // pinned readback
-  cudaStream_t copy_stream = nullptr;
-  cudaEvent_t copy_done = nullptr;
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-  bool timing_valid = false;
-  // ring of per-call event quadruples for dm_timing_sum
-  static constexpr uint32_t kRing = 1024;
-  cudaEvent_t* ring = nullptr;
-  uint32_t ring_n = 0;
-  cudaEvent_t* last_ev = nullptr;   // quadruple of the last timed call
-  dm_tuning tuning{};
-  // batched table merges: side streams, fork/join events, graph cache
-  static constexpr uint32_t kTableStreams = 4;
-  cudaStream_t side[kTableStreams] = {};
-  cudaEvent_t fork = nullptr;
-  cudaEvent_t join[kTableStreams] = {};
-  struct GraphEntry {
-    std::string key;
-    cudaGraphExec_t exec = nullptr;
-    uint64_t launches = 0;   // kernels in the graph
-    uint64_t last_use = 0;
-  };
-  std::vector<GraphEntry> graphs;
-  uint64_t graph_clock = 0;
-  cudaStream_t capture = nullptr;   // graphs are recorded here, never on a caller's stream
-  cudaError_t last_error = cudaSuccess;
-  uint64_t launches = 0;
-};
+#include "dm_ctx.h"
 
 namespace {
 
@@ -320,7 +287,7 @@ dm_status dm_create(dm_ctx** out, int device, size_t arena_bytes) {
 void dm_destroy(dm_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
-  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->arena && ctx->owns_arena) cudaFree(ctx->arena);
   if (ctx->status) cudaFree(ctx->status);
   if (ctx->host_status) cudaFreeHost(ctx->host_status);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -348,9 +315,10 @@ dm_status dm_reserve(dm_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->arena_bytes) return DM_OK;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return DM_ECUDA;
-  if (ctx->arena) cudaFree(ctx->arena);
+  if (ctx->arena && ctx->owns_arena) cudaFree(ctx->arena);
   ctx->arena = nullptr;
   ctx->arena_bytes = 0;
+  ctx->owns_arena = true;
   void* p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -362,6 +330,17 @@ dm_status dm_reserve(dm_ctx* ctx, size_t bytes) {
 }
 
 size_t dm_arena_bytes(const dm_ctx* ctx) { return ctx ? ctx->arena_bytes : 0; }
+
+}  // extern "C"
+
+void dm_ctx_use_region(dm_ctx* ctx, void* ptr, size_t bytes) {
+  if (ctx->arena && ctx->owns_arena) cudaFree(ctx->arena);
+  ctx->arena = ptr;
+  ctx->arena_bytes = bytes;
+  ctx->owns_arena = false;
+}
+
+extern "C" {
 
 uint64_t dm_launch_count(const dm_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
@@ -402,7 +381,7 @@ dm_status record_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, cons
     if (cudaStreamWaitEvent(ctx->side[i], ctx->fork, 0) != cudaSuccess) return DM_ECUDA;
   for (uint32_t c = 0; c < ncols; ++c) {
     const uint32_t i = c % S;
-    const uint32_t cap = dm::step1_capacity(in[c].value_bytes, ctx->sm_count) / S;
+    const uint32_t cap = dm::step1_capacity(in[c].value_bytes, ctx->sm_count) / (S * ctx->coop_share);
     void* base = static_cast<char*>(ctx->arena) + (size_t)i * region;
     dm_status st = run_column(ctx, &in[c], &out[c], base, ctx->side[i], flags, nullptr, &plans[c], cap ? cap : 1);
     if (st != DM_OK) return st;
@@ -449,6 +428,7 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
   put(&flags, sizeof(flags));
   put(&ctx->arena, sizeof(ctx->arena));
   put(&ctx->tuning, sizeof(ctx->tuning));
+  put(&ctx->coop_share, sizeof(ctx->coop_share));
   for (uint32_t c = 0; c < ncols; ++c) {
     put(&in[c], sizeof(dm_column_in));
     put(&out[c], sizeof(dm_column_out));

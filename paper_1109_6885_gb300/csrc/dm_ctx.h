@@ -1,0 +1,51 @@
+// The context object behind the opaque dm_ctx handle (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dmerge.h"
+
+struct dm_ctx {
+  int device = 0;
+  uint32_t sm_count = 0;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  uint32_t* status = nullptr;      // device status word
+  uint32_t* host_status = nullptr; // pinned readback
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t copy_done = nullptr;
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool timing_valid = false;
+  // ring of per-call event quadruples for dm_timing_sum
+  static constexpr uint32_t kRing = 1024;
+  cudaEvent_t* ring = nullptr;
+  uint32_t ring_n = 0;
+  cudaEvent_t* last_ev = nullptr;   // quadruple of the last timed call
+  dm_tuning tuning{};
+  // batched table merges: side streams, fork/join events, graph cache
+  static constexpr uint32_t kTableStreams = 4;
+  cudaStream_t side[kTableStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kTableStreams] = {};
+  struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;   // kernels in the graph
+    uint64_t last_use = 0;
+  };
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_clock = 0;
+  cudaStream_t capture = nullptr;   // graphs are recorded here, never on a caller's stream
+  cudaError_t last_error = cudaSuccess;
+  bool owns_arena = true;           // false: the arena is a region lent by a server
+  uint32_t coop_share = 1;          // cooperative Step 1 grids get capacity / (branches * coop_share)
+  uint64_t launches = 0;
+};
+
+
+// Lend a region of device memory to a context as its arena (not owned).
+void dm_ctx_use_region(dm_ctx* ctx, void* ptr, size_t bytes);

@@ -35,6 +35,9 @@ EXPORTS = [
     "dm_table_scratch_bytes", "dm_merge_column_host", "dm_host_scratch_bytes", "dm_sort_delta",
     "dm_merge_dicts", "dm_reencode", "dm_sync_status", "dm_last_timing", "dm_timing_sum",
     "dm_launch_count", "dm_merge_dicts_noalloc", "dm_set_tuning", "dm_get_tuning", "dm_last_error",
+    "dm_server_create", "dm_server_destroy", "dm_server_add_table", "dm_server_submit",
+    "dm_server_drain", "dm_server_request_info", "dm_server_stats_get", "dm_server_table_version",
+    "dm_sched_simulate",
     "dm_status_str",
 ]
 
@@ -68,6 +71,31 @@ class Tuning(ctypes.Structure):
         ("reencode_obufs", ctypes.c_uint32),
         ("reserved", ctypes.c_uint32 * 5),
     ]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("scratch_budget", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("table_id", ctypes.c_uint32), ("status", ctypes.c_int32),
+                ("submit_ns", ctypes.c_uint64), ("admit_ns", ctypes.c_uint64),
+                ("done_ns", ctypes.c_uint64), ("footprint", ctypes.c_uint64),
+                ("slot", ctypes.c_uint32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("tuples", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("first_submit_ns", ctypes.c_uint64), ("last_done_ns", ctypes.c_uint64),
+                ("peak_scratch_bytes", ctypes.c_uint64), ("scratch_budget", ctypes.c_uint64),
+                ("peak_concurrency", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class ColumnOut(ctypes.Structure):
@@ -129,6 +157,16 @@ def _load():
             "dm_status_str": ([i32], ctypes.c_char_p),
             "dm_set_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
             "dm_last_error": ([vp], ctypes.c_char_p),
+            "dm_server_create": ([ctypes.POINTER(vp), i32, ctypes.POINTER(ServerConfig)], i32),
+            "dm_server_destroy": ([vp], None),
+            "dm_server_add_table": ([vp, u32, pin, u32, pout], i32),
+            "dm_server_submit": ([vp, u32, ctypes.POINTER(u64)], i32),
+            "dm_server_drain": ([vp, u64], i32),
+            "dm_server_request_info": ([vp, u64, ctypes.POINTER(RequestInfo)], i32),
+            "dm_server_stats_get": ([vp, ctypes.POINTER(ServerStats)], i32),
+            "dm_server_table_version": ([vp, u32], u64),
+            "dm_sched_simulate": ([u64, u32, u32, vp, vp, u64, vp, vp, vp, vp, vp,
+                                   ctypes.POINTER(u64), ctypes.POINTER(u32)], i32),
             "dm_get_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
             "dm_merge_dicts_noalloc": ([u32, vp, u64, vp, vp, u64, vp, vp, vp, vp, vp, vp, vp],
                                        i32),
@@ -424,3 +462,74 @@ def fetch(res: DeviceResult, w: int, n_out: int):
     xm = to_host(res.x_main, np.uint32) if res.x_main is not None else None
     xd = to_host(res.x_delta, np.uint32) if res.x_delta is not None else None
     return new_dict, xm, xd, packed, b, u
+
+
+# ------------------------------------------------------------------ served merges
+
+class Server:
+    """dm_server: resident tables, merge requests admitted with continuous batching."""
+
+    def __init__(self, device: int = 0, slots: int = 4, scratch_budget: int = 1 << 30,
+                 flags: int = 0):
+        self.handle = ctypes.c_void_p()
+        cfg = ServerConfig(slots, scratch_budget, flags)
+        _check(_load().dm_server_create(ctypes.byref(self.handle), device, ctypes.byref(cfg)),
+               "dm_server_create")
+
+    def close(self):
+        if self.handle:
+            _load().dm_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_table(self, table_id: int, cins, couts):
+        n = len(cins)
+        _check(_load().dm_server_add_table(self.handle, table_id, (ColumnIn * n)(*cins), n,
+                                           (ColumnOut * n)(*couts)), "dm_server_add_table")
+
+    def submit(self, table_id: int) -> int:
+        rid = ctypes.c_uint64(0)
+        _check(_load().dm_server_submit(self.handle, table_id, ctypes.byref(rid)),
+               "dm_server_submit")
+        return int(rid.value)
+
+    def drain(self, timeout_ms: int = 600_000):
+        _check(_load().dm_server_drain(self.handle, timeout_ms), "dm_server_drain")
+
+    def info(self, request_id: int) -> RequestInfo:
+        r = RequestInfo()
+        _check(_load().dm_server_request_info(self.handle, request_id, ctypes.byref(r)),
+               "dm_server_request_info")
+        return r
+
+    def stats(self) -> ServerStats:
+        st = ServerStats()
+        _check(_load().dm_server_stats_get(self.handle, ctypes.byref(st)), "dm_server_stats_get")
+        return st
+
+    def version(self, table_id: int) -> int:
+        return int(_load().dm_server_table_version(self.handle, table_id))
+
+
+def dm_sched_simulate(pool_bytes: int, slots: int, footprint, service_ns, req_table, arrival_ns):
+    """The server's admission rules on a fake clock (no GPU): returns
+    (admit_ns, done_ns, slot, peak_bytes, peak_running)."""
+    fp = np.ascontiguousarray(footprint, np.uint64)
+    sv = np.ascontiguousarray(service_ns, np.uint64)
+    rt = np.ascontiguousarray(req_table, np.uint32)
+    ar = np.ascontiguousarray(arrival_ns, np.uint64)
+    n = rt.size
+    admit = np.zeros(n, np.uint64)
+    done = np.zeros(n, np.uint64)
+    slot = np.zeros(n, np.uint32)
+    pb = ctypes.c_uint64(0)
+    pr = ctypes.c_uint32(0)
+    _check(_load().dm_sched_simulate(pool_bytes, slots, fp.size, _ptr(fp), _ptr(sv), n, _ptr(rt),
+                                     _ptr(ar), _ptr(admit), _ptr(done), _ptr(slot),
+                                     ctypes.byref(pb), ctypes.byref(pr)), "dm_sched_simulate")
+    return admit, done, slot, int(pb.value), int(pr.value)
