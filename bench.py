@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
-from paper_1109_6885_gb300 import traffic  # noqa: E402
+from paper_1109_6885_gb300 import shard, traffic  # noqa: E402
 
 METRIC = "merged tuples/s per column"
 UNIT = "tuples/s"
@@ -273,11 +273,9 @@ def run_gpu(args):
     per_step = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[args.steps])
     phase_ms, calls = ctx.timing_sum()
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * n_tuples * args.steps / (total_ms / 1e3)
+    # every rank merged its own column: all ranks' tuples over the slowest rank's time
+    value = shard.aggregate_rate(n_tuples * args.steps, total_ms / 1e3, "cuda")
+    total_ms = 1e3 * shard.max_over_ranks(total_ms / 1e3, "cuda")
 
     # roofline of the dominant kernel (Step 2(b) re-encode), bytes it must move
     reencode_ms = phase_ms[3] / max(calls, 1)
@@ -366,11 +364,7 @@ def run_e2e(dm, ctx, col, m, d, w, u, b_new, args, world, barrier):
         uu, bb = dm.dm_merge_column_host(ctx, cin, cout, stream)
     torch.cuda.synchronize()
     barrier()
-    el = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([el], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        el = float(t.item())
+    el = shard.max_over_ranks(time.perf_counter() - t0, "cuda")
     assert (uu, bb) == (u, b_new)
     h2d = m * w + col.main_packed.nbytes + d * w + col.delta_codes.nbytes
     d2h = u * w + dm.dm_packed_bytes(n_out, b_new) + 16
@@ -437,11 +431,7 @@ def run_table(args):
         if world > 1:
             torch.distributed.barrier()
         per = sorted(ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps))
-        total = ev[0].elapsed_time(ev[args.steps])
-        if world > 1:
-            t = torch.tensor([total], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
+        total = 1e3 * shard.max_over_ranks(ev[0].elapsed_time(ev[args.steps]) / 1e3, "cuda")
         return total, per
 
     launches0 = ctx.launches
