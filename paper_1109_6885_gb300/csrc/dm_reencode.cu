@@ -74,15 +74,26 @@ __device__ __forceinline__ void unpack32(const uint32_t (&w)[B > 0 ? B : 1], uin
       c[j] = 0;
     } else {
       const int bit = j * B, k = bit >> 5, s = bit & 31;
-      uint32_t v;
-      if (s + B <= 32) v = w[k] >> s;
-      else v = __funnelshift_r(w[k], w[(k + 1 < B) ? k + 1 : k], s);
-      c[j] = (B == 32) ? v : (v & ((1u << (B & 31)) - 1u));
+      if (B == 32) {
+        c[j] = w[k];
+      } else if (s + B == 32) {
+        c[j] = w[k] >> s;                                        // the word's top field
+      } else if (s + B < 32) {
+        // field below the top: move it to the top, take the high B bits
+        // (two multiplies, FMA pipe, instead of a shift and a mask)
+        c[j] = __umulhi(w[k] * (1u << ((32 - s - B) & 31)), 1u << (B & 31));
+      } else {
+        const uint32_t v = __funnelshift_r(w[k], w[(k + 1 < B) ? k + 1 : k], s);
+        c[j] = v & ((1u << (B & 31)) - 1u);
+      }
     }
   }
 }
 
-// 32 values of BO bits into BO words at `row` (shared memory).
+// 32 values of BO bits into BO words at `row` (shared memory).  Fields do
+// not overlap, so a field is added rather than ORed in: x * 2^s + word is
+// one multiply-add (FMA pipe) instead of a shift and an OR (ALU pipe).  The
+// part of a field that spills into the next word starts that word.
 template <int BO>
 __device__ __forceinline__ void pack32(const uint32_t (&x)[32], uint32_t* row) {
   if constexpr (BO == 0) {
@@ -90,12 +101,11 @@ __device__ __forceinline__ void pack32(const uint32_t (&x)[32], uint32_t* row) {
   } else {
     uint32_t o[BO];
 #pragma unroll
-    for (int k = 0; k < BO; ++k) o[k] = 0;
-#pragma unroll
     for (int j = 0; j < 32; ++j) {
       const int bit = j * BO, k = bit >> 5, s = bit & 31;
-      o[k] |= x[j] << s;
-      if (s + BO > 32) o[(k + 1 < BO) ? k + 1 : k] |= x[j] >> ((32 - s) & 31);
+      if (s == 0) o[k] = x[j];
+      else o[k] = x[j] * (1u << s) + o[k];
+      if (s + BO > 32) o[(k + 1 < BO) ? k + 1 : k] = x[j] >> ((32 - s) & 31);
     }
     if constexpr (BO % 4 == 0) {
 #pragma unroll
@@ -263,8 +273,8 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArg
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const uint32_t e = s_x[c[j] >> dshift];
-          const uint32_t y = e + ((c[j] & dmask) << 20);
-          x[j] = c[j] + (y & 0xFFFFFu) + (y >> 31);
+          const uint32_t y = (c[j] & dmask) * (1u << 20) + e;   // multiply-add: FMA pipe
+          x[j] = c[j] + (y & 0xFFFFFu) + __umulhi(y, 2u);        // y >> 31 on the FMA pipe
           many |= ((e >> 20) == DIR_MANY_TOP ? 1u : 0u) << j;
         }
         // codes in buckets with several steps read X_M itself

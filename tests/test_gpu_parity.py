@@ -481,3 +481,48 @@ def test_tuning_changes_nothing(warps, stages, obufs):
                                                seed=warps))
     assert_parity(c, small, dm.DM_FLAG_X_SMEM)
     c.close()
+
+
+@pytest.mark.parametrize("b_extra", [0, 1, 4])
+def test_reencode_directory_width_variants(ctx, b_extra):
+    """Directory mode over codes stored wider than needed (covering and not)."""
+    import torch
+    rng = np.random.default_rng(40 + b_extra)
+    m, k = 20_000, 400
+    xm, u = _steps_table(m, k, rng)
+    b, bo = synth.bits_for(m) + b_extra, synth.bits_for(u)
+    n_main = 1_200_001
+    mc = rng.integers(0, m, n_main).astype(np.uint32)
+    main = synth.pack(mc, b)
+    dc = np.zeros(1, np.uint32)
+    xd = np.zeros(1, np.uint32)
+    want = oracle.reencode(main, b, n_main, dc, xm, xd, bo)
+    out = torch.full((dm.dm_packed_bytes(n_main + 1, bo) // 4,), -1, dtype=torch.int32,
+                     device="cuda")
+    bits = torch.tensor([bo], dtype=torch.int32, device="cuda")
+    dm.dm_reencode(ctx, dm.to_device(main), b, n_main, dm.to_device(dc), 1, dm.to_device(xm), m,
+                   dm.to_device(xd), 1, bits, bo, out, None, dm.DM_FLAG_X_SMEM)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_OK
+    assert np.array_equal(dm.to_host(out, np.uint32), want)
+
+
+def test_directory_mode_flags_codes_past_the_dictionary(ctx):
+    """Codes >= |U_M| in a covering directory are flagged, clamped, never faulting."""
+    import torch
+    rng = np.random.default_rng(77)
+    m = 20_000
+    xm = np.arange(m, dtype=np.uint32)
+    b = synth.bits_for(m)
+    mc = rng.integers(0, m, 1_100_000).astype(np.uint32)
+    mc[::1000] = rng.integers(m, 2**b, mc[::1000].size)       # invalid codes
+    main = synth.pack(mc, b)
+    out = torch.zeros(dm.dm_packed_bytes(mc.size, b) // 4, dtype=torch.int32, device="cuda")
+    bits = torch.tensor([b], dtype=torch.int32, device="cuda")
+    dm.dm_reencode(ctx, dm.to_device(main), b, mc.size, None, 0, dm.to_device(xm), m, None, 0, bits,
+                   b, out, None, dm.DM_FLAG_X_SMEM)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_ECODE
+    got = np.array(_brute.unpack_bits(dm.to_host(out, np.uint32)[:2000], 1000, b))
+    want = np.minimum(mc[:1000], m - 1)
+    assert np.array_equal(got, want)
