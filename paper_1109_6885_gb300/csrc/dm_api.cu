@@ -122,7 +122,8 @@ dm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DM_OK : DM_ECUD
 // kernel and at the end (nullptr: no timing).
 dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* base,
                      cudaStream_t s, uint32_t flags, cudaEvent_t* ev, const dm::ReencodePlan* pre_plan = nullptr,
-                     uint32_t grid_cap = 0) {
+                     uint32_t grid_cap = 0, dm::ReencodePlan* plan_out = nullptr,
+                     dm::ReencodeArgs* args_out = nullptr) {
   const bool timing = ev != nullptr;
   ColumnScratch cs;
   carve_column(base, in, out, &cs);
@@ -178,6 +179,12 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
     cudaEventRecord(ev[1], s);
     cudaEventRecord(ev[2], s);
     cudaEventRecord(ev[3], s);
+  }
+  if (plan_out) {
+    // the caller launches Step 2(b) itself (in chunks)
+    *plan_out = plan;
+    if (args_out) *args_out = ra;
+    return DM_OK;
   }
   if (n_out) {
     e = dm::launch_reencode_planned(plan, ra, s, &ctx->launches);
@@ -265,7 +272,11 @@ dm_status dm_create(dm_ctx** out, int device, size_t arena_bytes) {
     }
   }
   bool ok = cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) == cudaSuccess &&
-            cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) == cudaSuccess;
+            cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&ctx->d2h_stream, cudaStreamNonBlocking) == cudaSuccess;
+  for (uint32_t i = 0; ok && i < dm_ctx::kChunks; ++i)
+    ok = cudaEventCreateWithFlags(&ctx->h2d_done[i], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ctx->comp_done[i], cudaEventDisableTiming) == cudaSuccess;
   for (uint32_t i = 0; ok && i < dm_ctx::kTableStreams; ++i)
     ok = cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking) == cudaSuccess &&
          cudaEventCreateWithFlags(&ctx->join[i], cudaEventDisableTiming) == cudaSuccess;
@@ -302,6 +313,11 @@ void dm_destroy(dm_ctx* ctx) {
   }
   if (ctx->fork) cudaEventDestroy(ctx->fork);
   if (ctx->capture) cudaStreamDestroy(ctx->capture);
+  if (ctx->d2h_stream) cudaStreamDestroy(ctx->d2h_stream);
+  for (uint32_t i = 0; i < dm_ctx::kChunks; ++i) {
+    if (ctx->h2d_done[i]) cudaEventDestroy(ctx->h2d_done[i]);
+    if (ctx->comp_done[i]) cudaEventDestroy(ctx->comp_done[i]);
+  }
   if (ctx->ring) {
     for (uint32_t i = 0; i < 5 * dm_ctx::kRing; ++i)
       if (ctx->ring[i]) cudaEventDestroy(ctx->ring[i]);
@@ -508,7 +524,7 @@ size_t dm_host_scratch_bytes(const dm_column_in* in, uint32_t flags) {
   b += align_up(m * w) + align_up(dm_packed_bytes(in->main_rows, in->main_bits));
   b += align_up(d * w) + align_up(in->delta_rows * 4);
   b += align_up((m + d) * w) + align_up(dm_packed_bytes(n_out, bits_for(m + d)));
-  b += align_up(m * 4) + align_up(d * 4) + align_up(16) + align_up((size_t)dm::reencode_dir_words() * 4);
+  b += align_up(m * 4) + align_up(d * 4) + align_up(16);
   return b + dm_scratch_bytes(in, flags);
 }
 
@@ -537,7 +553,6 @@ dm_status dm_merge_column_host(dm_ctx* ctx, const dm_column_in* in, const dm_col
   dout.x_main = static_cast<uint32_t*>(c.take(m * 4));
   dout.x_delta = static_cast<uint32_t*>(c.take(d * 4));
   char* scal = static_cast<char*>(c.take(16));
-  uint32_t* xdir = static_cast<uint32_t*>(c.take((size_t)dm::reencode_dir_words() * 4));
   dout.d_new_dict_len = reinterpret_cast<uint64_t*>(scal);
   dout.d_new_bits = reinterpret_cast<uint32_t*>(scal + 8);
   void* scratch = c.take(0);
@@ -547,72 +562,92 @@ dm_status dm_merge_column_host(dm_ctx* ctx, const dm_column_in* in, const dm_col
   din.delta_codes = static_cast<const uint32_t*>(p_dcodes);
 
   cudaError_t e = cudaSuccess;
-  // dictionaries and delta codes on the merge stream; the large main stream
-  // on the copy stream so that its upload overlaps Steps 1(a) and 1(b)
+  // On any failure the side streams are drained first: the caller's host
+  // buffers are free again once this call returns.
+  auto fail = [&](cudaError_t err, dm_status code) {
+    if (err != cudaSuccess) ctx->last_error = err;
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamSynchronize(ctx->d2h_stream);
+    cudaStreamSynchronize(s);
+    return code;
+  };
+  // The main vector goes up in chunks of whole 1024-row tiles on the copy
+  // stream from the start (overlapping Steps 1(a), 1(b)); each chunk is
+  // re-encoded as soon as it has landed and its output comes back on a
+  // third stream while later chunks are still being uploaded or encoded.
+  const uint64_t nm = in->main_rows;
+  uint32_t K = dm_ctx::kChunks;
+  uint64_t per = ((nm + K - 1) / K + 1023) / 1024 * 1024;
+  if (per == 0) per = 1024;
+  K = (uint32_t)std::max<uint64_t>(1, (nm + per - 1) / per);
+  auto chunk_lo = [&](uint32_t k) { return std::min<uint64_t>(nm, (uint64_t)k * per); };
+  auto chunk_hi = [&](uint32_t k) { return k + 1 == K ? nm : std::min<uint64_t>(nm, (uint64_t)(k + 1) * per); };
+  const uint32_t b = in->main_bits;
+
   if (m) e = cudaMemcpyAsync(p_main_dict, in->main_dict, m * w, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && d) e = cudaMemcpyAsync(p_ddict, in->delta_dict, d * w, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && in->delta_rows)
     e = cudaMemcpyAsync(p_dcodes, in->delta_codes, in->delta_rows * 4, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && main_bytes) {
-    e = cudaEventRecord(ctx->copy_done, s);  // copy stream starts after earlier work on s
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_done, 0);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(p_main, in->main_packed, main_bytes, cudaMemcpyHostToDevice, ctx->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->copy_done, s);   // later streams start after earlier work on s
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_done, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->d2h_stream, ctx->copy_done, 0);
+  for (uint32_t k = 0; e == cudaSuccess && k < K; ++k) {
+    const uint64_t w0 = chunk_lo(k) * b / 32;
+    const uint64_t w1 = k + 1 == K ? main_bytes / 4 : chunk_hi(k) * b / 32;
+    if (w1 > w0)
+      e = cudaMemcpyAsync(static_cast<uint32_t*>(p_main) + w0, static_cast<const uint32_t*>(in->main_packed) + w0,
+                          (w1 - w0) * 4, cudaMemcpyHostToDevice, ctx->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->h2d_done[k], ctx->copy_stream);
   }
-  if (e != cudaSuccess) return DM_ECUDA;
+  if (e != cudaSuccess) return fail(e, DM_ECUDA);
 
-  // Steps 1(a), 1(b)+2(a) on s (overlapping the main upload), then 2(b)
-  dm_column_in stage1 = din;
-  stage1.main_rows = 0;
-  stage1.delta_rows = 0;
-  st = run_column(ctx, &stage1, &dout, scratch, s, flags, nullptr);
-  if (st != DM_OK) return st;
-  if (main_bytes) {
-    if (cudaEventRecord(ctx->copy_done, ctx->copy_stream) != cudaSuccess ||
-        cudaStreamWaitEvent(s, ctx->copy_done, 0) != cudaSuccess)
-      return DM_ECUDA;
-  }
-  if (n_out) {
-    // X tables now live in dout; re-encode only
-    dm::ReencodeArgs ra{};
-    ra.main_words = static_cast<const uint32_t*>(din.main_packed);
-    ra.main_words_n = main_bytes / 4;
-    ra.n_main = din.main_rows;
-    ra.dcodes = din.delta_codes;
-    ra.n_delta = din.delta_rows;
-    ra.xm = dout.x_main;
-    ra.m = (uint32_t)m;
-    ra.xd = dout.x_delta;
-    ra.d = (uint32_t)d;
-    ra.d_bits = dout.d_new_bits;
-    ra.max_bits = bits_for(m + d);
-    ra.out_words = static_cast<uint32_t*>(dout.new_packed);
-    ra.status = ctx->status;
-    ra.xdir = xdir;
-    ra.tune_warps = ctx->tuning.reencode_warps;
-    ra.tune_stages = ctx->tuning.reencode_stages;
-    ra.tune_obufs = ctx->tuning.reencode_obufs;
-    e = dm::launch_reencode(din.main_bits, ra, s, ctx->sm_count, flags, &ctx->launches);
-    if (e != cudaSuccess) return DM_ECUDA;
-  }
+  // Steps 1(a), 1(b), 2(a) and the X_M directory (one kernel) on s
+  dm::ReencodePlan plan{};
+  dm::ReencodeArgs ra{};
+  st = run_column(ctx, &din, &dout, scratch, s, flags, nullptr, nullptr, 0, &plan, &ra);
+  if (st != DM_OK) return fail(cudaSuccess, st);
+  // the new width fixes where each chunk's output starts: read it back
   uint64_t hs[2] = {0, 0};
   e = cudaMemcpyAsync(hs, scal, 16, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return DM_ECUDA;
+  if (e != cudaSuccess) return fail(e, DM_ECUDA);
   const uint64_t u = hs[0];
   const uint32_t bn = (uint32_t)(hs[1] & 0xFFFFFFFFu);
-  if (u > m + d || bn > 32) return DM_ETIMEOUT;
+  if (u > m + d || bn > 32) return fail(cudaSuccess, DM_ETIMEOUT);
   *new_dict_len = u;
   *new_bits = bn;
-  if (u) e = cudaMemcpyAsync(out->new_dict, dout.new_dict, u * w, cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess && n_out && bn)
-    e = cudaMemcpyAsync(out->new_packed, dout.new_packed, dm_packed_bytes(n_out, bn), cudaMemcpyDeviceToHost, s);
+  if (u) e = cudaMemcpyAsync(out->new_dict, dout.new_dict, u * w, cudaMemcpyDeviceToHost, ctx->d2h_stream);
   if (e == cudaSuccess && out->x_main && m)
-    e = cudaMemcpyAsync(out->x_main, dout.x_main, m * 4, cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(out->x_main, dout.x_main, m * 4, cudaMemcpyDeviceToHost, ctx->d2h_stream);
   if (e == cudaSuccess && out->x_delta && d)
-    e = cudaMemcpyAsync(out->x_delta, dout.x_delta, d * 4, cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(out->x_delta, dout.x_delta, d * 4, cudaMemcpyDeviceToHost, ctx->d2h_stream);
+
+  const uint64_t out_words_total = dm_packed_bytes(n_out, bn) / 4;
+  for (uint32_t k = 0; e == cudaSuccess && n_out && k < K; ++k) {
+    const uint64_t r0 = chunk_lo(k), r1 = chunk_hi(k);
+    const bool last = k + 1 == K;
+    dm::ReencodeArgs rc = ra;
+    rc.main_words = ra.main_words + r0 * b / 32;
+    rc.main_words_n = (last ? main_bytes / 4 : r1 * b / 32) - r0 * b / 32;
+    rc.n_main = r1 - r0;
+    rc.n_delta = last ? in->delta_rows : 0;
+    rc.out_words = ra.out_words + r0 * bn / 32;
+    if (rc.n_main + rc.n_delta == 0) continue;
+    e = cudaStreamWaitEvent(s, ctx->h2d_done[k], 0);
+    if (e == cudaSuccess) e = dm::launch_reencode_planned(plan, rc, s, &ctx->launches);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->comp_done[k], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->d2h_stream, ctx->comp_done[k], 0);
+    const uint64_t o0 = r0 * bn / 32, o1 = last ? out_words_total : r1 * bn / 32;
+    if (e == cudaSuccess && bn && o1 > o0)
+      e = cudaMemcpyAsync(static_cast<uint32_t*>(out->new_packed) + o0, ra.out_words + o0, (o1 - o0) * 4,
+                          cudaMemcpyDeviceToHost, ctx->d2h_stream);
+  }
+  if (e != cudaSuccess) return fail(e, DM_ECUDA);
+  e = cudaStreamSynchronize(ctx->d2h_stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  return cuda_status(e);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->copy_stream);
+  if (e != cudaSuccess) return fail(e, DM_ECUDA);
+  return DM_OK;
 }
 
 dm_status dm_sort_delta(dm_ctx* ctx, uint32_t w, const void* delta_dict, uint64_t d, void* ud_out,

@@ -18,6 +18,11 @@ struct dm_ctx {
   uint32_t* host_status = nullptr; // pinned readback
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_done = nullptr;
+  // host-buffer merges: main upload and result download in chunks
+  static constexpr uint32_t kChunks = 8;
+  cudaStream_t d2h_stream = nullptr;
+  cudaEvent_t h2d_done[kChunks] = {};
+  cudaEvent_t comp_done[kChunks] = {};
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
   bool timing_valid = false;
   // ring of per-call event quadruples for dm_timing_sum

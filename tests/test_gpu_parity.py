@@ -296,20 +296,36 @@ def test_argument_errors(ctx):
 
 # ------------------------------------------------------------------ other entry points
 
-def test_host_buffer_entry_point(ctx):
-    col = synth.make_column(synth.ColumnSpec(n_main=400_003, m=30_000, w=16, n_delta=20_000,
-                                             f_new=0.4, dist="zipf", seed=21))
+# (n_main, m, w, n_delta, f_new, dist): the main vector goes up and the
+# result comes back in chunks of whole 1024-row tiles; the cases cover a
+# ragged last chunk, an exact multiple, a single short chunk, a delta longer
+# than the main vector, the X_M directory lookup, and a zero-width column.
+HOST_CASES = [
+    (400_003, 30_000, 16, 20_000, 0.4, "zipf"),
+    (8 * 1024 * 3, 100, 8, 5_000, 0.9, "uniform"),
+    (1_000, 5, 4, 3_000, 0.5, "uniform"),
+    (2_000_001, 70_000, 8, 100_000, 0.3, "zipf"),
+    (1_500_001, 1, 4, 0, 0.0, "uniform"),
+    (3_000_000, 200, 4, 4_096, 0.0, "zipf"),
+]
+
+
+@pytest.mark.parametrize("case", HOST_CASES)
+def test_host_buffer_entry_point(ctx, case):
+    n_main, m0, w, n_delta, f_new, dist = case
+    col = synth.make_column(synth.ColumnSpec(n_main=n_main, m=m0, w=w, n_delta=n_delta,
+                                             f_new=f_new, dist=dist, seed=21 + n_main % 97))
     ref = oracle.merge_synth_column(col)
     cin = dm.ColumnIn(col.w, col.main_dict.ctypes.data, col.main_dict.shape[0],
                       col.main_packed.ctypes.data, col.main_bits, col.n_main,
                       col.delta_dict.ctypes.data, col.delta_dict.shape[0],
                       col.delta_codes.ctypes.data, col.n_delta)
     m, d = col.main_dict.shape[0], col.delta_dict.shape[0]
-    new_dict = synth.key_array(m + d, 16)
-    packed = np.zeros(dm.dm_packed_bytes(col.n_main + col.n_delta, dm.dm_bits_for(m + d)) // 4,
-                      np.uint32)
-    xm = np.zeros(m, np.uint32)
-    xd = np.zeros(d, np.uint32)
+    new_dict = synth.key_array(max(m + d, 1), w)
+    nwords = dm.dm_packed_bytes(col.n_main + col.n_delta, dm.dm_bits_for(m + d)) // 4
+    packed = np.full(max(nwords, 1), 0xDEADBEEF, np.uint32)
+    xm = np.zeros(max(m, 1), np.uint32)
+    xd = np.zeros(max(d, 1), np.uint32)
     cout = dm.ColumnOut(new_dict.ctypes.data, packed.ctypes.data, xm.ctypes.data, xd.ctypes.data,
                         None, None)
     ctx.reserve(dm.dm_host_scratch_bytes(cin))
@@ -318,7 +334,7 @@ def test_host_buffer_entry_point(ctx):
     assert u == ref.u and b == ref.new_bits
     assert np.array_equal(new_dict[:u], ref.new_dict)
     assert np.array_equal(packed[:ref.new_packed.size], ref.new_packed)
-    assert np.array_equal(xm, ref.x_main) and np.array_equal(xd, ref.x_delta)
+    assert np.array_equal(xm[:m], ref.x_main) and np.array_equal(xd[:d], ref.x_delta)
 
 
 def _table(rng, ncols, n_main, n_delta, max_m, config=4):
