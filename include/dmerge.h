@@ -308,7 +308,9 @@ typedef struct {
   uint32_t reencode_warps;   /* Step 2(b): warps per block (1..16) */
   uint32_t reencode_stages;  /* Step 2(b): input bulk-copy stages per warp (2..4) */
   uint32_t reencode_obufs;   /* Step 2(b): output staging buffers per warp (1..2) */
-  uint32_t reserved[5];
+  uint32_t host_chunks;      /* dm_merge_column_host: pieces the main vector is
+                                uploaded, re-encoded and downloaded in (1..32) */
+  uint32_t reserved[4];
 } dm_tuning;
 
 dm_status dm_set_tuning(dm_ctx* ctx, const dm_tuning* tuning);

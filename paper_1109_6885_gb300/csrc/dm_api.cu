@@ -576,7 +576,7 @@ dm_status dm_merge_column_host(dm_ctx* ctx, const dm_column_in* in, const dm_col
   // re-encoded as soon as it has landed and its output comes back on a
   // third stream while later chunks are still being uploaded or encoded.
   const uint64_t nm = in->main_rows;
-  uint32_t K = dm_ctx::kChunks;
+  uint32_t K = ctx->tuning.host_chunks ? ctx->tuning.host_chunks : dm_ctx::kDefaultChunks;
   uint64_t per = ((nm + K - 1) / K + 1023) / 1024 * 1024;
   if (per == 0) per = 1024;
   K = (uint32_t)std::max<uint64_t>(1, (nm + per - 1) / per);
@@ -741,7 +741,7 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
 dm_status dm_set_tuning(dm_ctx* ctx, const dm_tuning* t) {
   if (!ctx || !t) return DM_EINVAL;
   if (t->reencode_warps > 16 || (t->reencode_stages && (t->reencode_stages < 2 || t->reencode_stages > 4)) ||
-      t->reencode_obufs > 2)
+      t->reencode_obufs > 2 || t->host_chunks > dm_ctx::kChunks)
     return DM_EINVAL;
   ctx->tuning = *t;
   return DM_OK;

@@ -19,7 +19,7 @@ struct dm_ctx {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t copy_done = nullptr;
   // host-buffer merges: main upload and result download in chunks
-  static constexpr uint32_t kChunks = 8;
+  static constexpr uint32_t kChunks = 32, kDefaultChunks = 8;
   cudaStream_t d2h_stream = nullptr;
   cudaEvent_t h2d_done[kChunks] = {};
   cudaEvent_t comp_done[kChunks] = {};

@@ -69,7 +69,8 @@ class Tuning(ctypes.Structure):
         ("reencode_warps", ctypes.c_uint32),
         ("reencode_stages", ctypes.c_uint32),
         ("reencode_obufs", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 5),
+        ("host_chunks", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 4),
     ]
 
 
@@ -261,9 +262,13 @@ class Context:
         return int(_load().dm_launch_count(self.handle))
 
     def set_tuning(self, **kw):
-        """Launch parameters (reencode_warps, reencode_stages, reencode_obufs; 0 = default)."""
+        """Launch parameters (reencode_warps, reencode_stages, reencode_obufs,
+        host_chunks; 0 = default)."""
         t = self.get_tuning()
+        names = {f[0] for f in Tuning._fields_} - {"reserved"}
         for k, v in kw.items():
+            if k not in names:
+                raise TypeError(f"unknown tuning field {k!r}")
             setattr(t, k, int(v))
         _check(_load().dm_set_tuning(self.handle, ctypes.byref(t)), "dm_set_tuning")
 

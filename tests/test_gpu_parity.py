@@ -337,6 +337,32 @@ def test_host_buffer_entry_point(ctx, case):
     assert np.array_equal(xm[:m], ref.x_main) and np.array_equal(xd[:d], ref.x_delta)
 
 
+@pytest.mark.parametrize("chunks", [1, 3, 32])
+def test_host_buffer_chunk_counts(chunks):
+    """The chunk count splits the copies and launches, never the result."""
+    col = synth.make_column(synth.ColumnSpec(n_main=1_234_567, m=40_000, w=8, n_delta=30_000,
+                                             f_new=0.3, dist="zipf", seed=77))
+    ref = oracle.merge_synth_column(col)
+    c = dm.Context(0, 1 << 20)
+    c.set_tuning(host_chunks=chunks)
+    cin = dm.ColumnIn(col.w, col.main_dict.ctypes.data, col.main_dict.shape[0],
+                      col.main_packed.ctypes.data, col.main_bits, col.n_main,
+                      col.delta_dict.ctypes.data, col.delta_dict.shape[0],
+                      col.delta_codes.ctypes.data, col.n_delta)
+    m, d = col.main_dict.shape[0], col.delta_dict.shape[0]
+    new_dict = synth.key_array(m + d, 8)
+    packed = np.zeros(dm.dm_packed_bytes(col.n_main + col.n_delta, dm.dm_bits_for(m + d)) // 4,
+                      np.uint32)
+    cout = dm.ColumnOut(new_dict.ctypes.data, packed.ctypes.data, None, None, None, None)
+    c.reserve(dm.dm_host_scratch_bytes(cin))
+    u, b = dm.dm_merge_column_host(c, cin, cout)
+    assert c.sync_status() == dm.DM_OK
+    c.close()
+    assert u == ref.u and b == ref.new_bits
+    assert np.array_equal(new_dict[:u], ref.new_dict)
+    assert np.array_equal(packed[:ref.new_packed.size], ref.new_packed)
+
+
 def _table(rng, ncols, n_main, n_delta, max_m, config=4):
     cols, dcols, results = [], [], []
     for j in range(ncols):
