@@ -446,10 +446,14 @@ def _steps_table(m, k, rng, clustered=False):
 
 @pytest.mark.parametrize("m,k,clustered", [(20_000, 0, False), (20_000, 150, False),
                                            (20_000, 20_000, False), (300_000, 3_000, True),
-                                           (1_000_000, 3_000, False), (1_000_000, 300_000, False),
-                                           (5_000_000, 40_000, False)])
+                                           (1_000_000, 3_000, False), (1_000_000, 30_000, False),
+                                           (1_000_000, 300_000, False), (100_000, 25_000, True),
+                                           (16_385, 900, True), (1 << 20, 5_000, False),
+                                           ((1 << 20) + 1, 5_000, False), (5_000_000, 40_000, False)])
 def test_reencode_directory_mode(ctx, m, k, clustered):
-    """X_M looked up through the shared-memory directory (forced) vs the oracle."""
+    """X_M looked up through the shared-memory directory (forced) vs the oracle.  The cases
+    run from no steps to several per bucket (those buckets read X_M itself), with new
+    values that share an insertion point (clustered)."""
     import torch
     rng = np.random.default_rng(m + k)
     xm, u = _steps_table(m, k, rng, clustered)
@@ -474,6 +478,7 @@ def test_reencode_directory_mode(ctx, m, k, clustered):
 
 @pytest.mark.parametrize("m,n_delta,f_new,pool", [(50_000, 20_000, 0.3, None),
                                                    (400_000, 100_000, 0.5, 0),
+                                                   (1_000_000, 200_000, 0.3, 30_000),
                                                    (2_000_000, 50_000, 0.3, None)])
 def test_merge_column_directory_mode(ctx, m, n_delta, f_new, pool):
     spec = synth.ColumnSpec(n_main=3_000_001, m=m, w=8, n_delta=n_delta, f_new=f_new, pool=pool,
