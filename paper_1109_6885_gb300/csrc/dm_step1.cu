@@ -5,24 +5,26 @@
 //
 // Step 1(a).  The paper walks the leaves of a CSB+ tree kept during inserts
 // (Section 5.1); with the delta dictionary stored as an insertion-order
-// array, Step 1(a) is a stable LSD radix sort of (key, insertion code)
-// pairs, 8-bit digits, perm[j] = insertion code of U_D[j] being the tuple-id
-// map of Section 5.3.  One sweep counts the digits of every pass; each block
-// then derives the plan (first slot of every digit, passes whose digit is
-// not constant).  Each pass ranks 2048-key tiles in shared memory with a
-// stable warp multisplit (ballots over the digit bits), finds the tile's
-// offset per digit by decoupled look-back over earlier tiles, stages the
-// tile in digit order and writes it out coalesced.
+// array, Step 1(a) sorts (key, insertion code) pairs, perm[j] = insertion
+// code of U_D[j] being the tuple-id map of Section 5.3.  One sweep counts
+// the 8-bit digits of every byte; each block then derives the plan (first
+// slot of every digit, bytes whose digit is not constant).  When every
+// bucket of the most significant varying byte holds at most 2048 keys, one
+// partition pass scatters the keys into those buckets (atomic cursors) and
+// each bucket is merge-sorted in shared memory by (key, insertion code);
+// otherwise stable LSD passes run, each ranking 1024-key tiles with a warp
+// multisplit and a decoupled look-back over earlier tiles.
 //
 // Step 1(b).  The paper cuts both dictionaries at N_T-quantiles and fixes
 // the output offsets with a counter array and a prefix sum (Section 6.2.1).
 // Here tile t owns merged positions [2048t, 2048t + 2048): a merge-path
-// (co-rank) search cuts U_M and U_D, each thread merges 8 positions out of
-// shared memory (ties: the main value first), a position is a duplicate
-// when its key equals the previous one in merged order (values in both
-// dictionaries and repeats inside D_dict alike), and its new code is the
-// number of non-duplicates at or before it minus one, from a block scan
-// plus a decoupled look-back.  U'[code] receives each non-duplicate, X_M /
+// (co-rank) search cuts U_M and U_D (ties: the main value first).  Inside
+// the tile, each U_D entry is ranked against the U_M segment by binary
+// search; a U_D entry is a duplicate when it equals the key before it in
+// merged order (a value in both dictionaries, or a repeat inside D_dict; a
+// U_M entry never is), and every position's new code follows from the
+// ranks and one block scan of the non-duplicates, plus the tile's offset
+// from a decoupled look-back.  U'[code] receives each non-duplicate, X_M /
 // X_D every position; the last tile publishes |U'| and E'_C = ceil(log2|U'|).
 //
 // The phases are separated by grid-wide barriers (bounded spins); the
@@ -103,23 +105,25 @@ template <int W>
 struct MergeSmem {
   using K = typename KeyOf<W>::T;
   K keys[S1_TILE];                 // U_M segment then U_D segment
-  K last[S1_THREADS];
-  uint32_t perm[S1_TILE];
+  uint32_t perm[S1_TILE];          // insertion codes of the U_D segment
+  uint32_t rank[S1_TILE];          // per U_D entry: U_M entries of the tile at or below it
+  alignas(16) uint32_t cnt[S1_TILE];   // per U_M entry: U_D entries placed right before it, then the prefix
+  uint32_t ndx[S1_TILE + 1];       // per U_D entry: non-duplicate U_D entries before it (and the total)
   uint32_t wsum[S1_WARPS];
   uint64_t cut[2];
   uint64_t excl, lb_sum;
   uint32_t nearest;
-  K pred, prevA, prevB;
+  K prevA, prevB;
 };
 
-constexpr uint32_t BK_CAP = 2048;   // keys a block sorts in shared memory at once
-constexpr uint32_t BK_SINGLE = 512; // at most this many keys: one block sorts them all
+constexpr uint32_t BK_CAP = 2048;     // keys a block sorts in shared memory at once
+constexpr uint32_t BK_SINGLE = BK_CAP;  // at most this many keys: one block sorts them all
 
 template <int W>
 struct BucketSmem {
   using K = typename KeyOf<W>::T;
-  K keys[BK_CAP];
-  uint32_t vals[BK_CAP];
+  K keys[2][BK_CAP + BK_CAP / 16];   // ping-pong buffers of the merge rounds (bk_slot layout)
+  uint32_t vals[2][BK_CAP + BK_CAP / 16];
 };
 
 template <int W>
@@ -136,7 +140,10 @@ constexpr size_t step1_smem_bytes() {
 }
 
 // ---------------------------------------------------------------- Step 1(a)
-// Digit counts of every pass (blocks below hist_blocks take part).
+// Digit counts of every pass (blocks below hist_blocks take part; each
+// thread loads HI_ITEMS keys at once, then counts them in shared memory).
+constexpr uint32_t HI_ITEMS = 8;
+
 template <int W>
 __device__ void hist_phase(const Step1Args& a, uint32_t* sh) {
   using K = typename KeyOf<W>::T;
@@ -144,11 +151,21 @@ __device__ void hist_phase(const Step1Args& a, uint32_t* sh) {
   for (uint32_t i = threadIdx.x; i < W * 256; i += S1_THREADS) sh[i] = 0;
   __syncthreads();
   const K* keys = static_cast<const K*>(a.in_keys);
-  for (uint64_t idx = (uint64_t)blockIdx.x * S1_THREADS + threadIdx.x; idx < a.d;
-       idx += (uint64_t)a.hist_blocks * S1_THREADS) {
-    const K k = load_key(keys + idx);
+  const uint64_t stride = (uint64_t)a.hist_blocks * S1_THREADS * HI_ITEMS;
+  for (uint64_t base = (uint64_t)blockIdx.x * S1_THREADS * HI_ITEMS + threadIdx.x; base < a.d; base += stride) {
+    K k[HI_ITEMS];
 #pragma unroll
-    for (int p = 0; p < W; ++p) atomicAdd(&sh[p * 256 + key_digit(k, p)], 1u);
+    for (int q = 0; q < (int)HI_ITEMS; ++q) {
+      const uint64_t idx = base + (uint64_t)q * S1_THREADS;
+      if (idx < a.d) k[q] = load_key(keys + idx);
+    }
+#pragma unroll
+    for (int q = 0; q < (int)HI_ITEMS; ++q) {
+      if (base + (uint64_t)q * S1_THREADS < a.d) {
+#pragma unroll
+        for (int p = 0; p < W; ++p) atomicAdd(&sh[p * 256 + key_digit(k[q], p)], 1u);
+      }
+    }
   }
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < W * 256; i += S1_THREADS)
@@ -345,49 +362,182 @@ __device__ void pass_tile(const Step1Args& a, int pass, uint32_t tile, int e, co
   __syncthreads();
 }
 
+// One tile of the MSD partition on digit `top`: the input dictionary's keys
+// go to their digit's bucket (its first slot from the plan), each tile
+// claiming a run of every bucket with one atomic add on that bucket's cursor
+// (zeroed).  The order inside a bucket is arbitrary; the bucket sort that
+// follows orders by (key, insertion code).
+template <int W>
+__device__ void msd_tile(const Step1Args& a, int top, uint32_t tile, const uint32_t* s_plan, SortSmem<W>& S) {
+  using K = typename KeyOf<W>::T;
+  const uint32_t tid = threadIdx.x;
+  const uint64_t d = a.d;
+  const K* src = static_cast<const K*>(a.in_keys);
+  K* dst_k = static_cast<K*>(a.keys[0]);
+  uint32_t* dst_v = a.vals[0];
+  uint32_t* cursor = a.sort_lb;
+  S.tstart[tid] = 0;   // per-digit count of this tile
+  __syncthreads();
+  const uint64_t tbase = (uint64_t)tile * SR_TILE + tid;
+  K key[SR_ITEMS];
+  uint32_t dig[SR_ITEMS], rank[SR_ITEMS];
+#pragma unroll
+  for (int r = 0; r < (int)SR_ITEMS; ++r) {
+    const uint64_t idx = tbase + (uint64_t)r * S1_THREADS;
+    dig[r] = 256;
+    if (idx < d) key[r] = load_key(src + idx);
+  }
+#pragma unroll
+  for (int r = 0; r < (int)SR_ITEMS; ++r) {
+    if (tbase + (uint64_t)r * S1_THREADS < d) {
+      dig[r] = key_digit(key[r], top);
+      rank[r] = atomicAdd(&S.tstart[dig[r]], 1u);
+    }
+  }
+  __syncthreads();
+  const uint32_t c = S.tstart[tid];
+  if (c) S.gbase[tid] = s_plan[top * 256 + tid] + atomicAdd(&cursor[tid], c);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < (int)SR_ITEMS; ++r) {
+    if (dig[r] < 256) {
+      const uint64_t pos = (uint64_t)S.gbase[dig[r]] + rank[r];
+      if (pos < d) {
+        dst_k[pos] = key[r];
+        dst_v[pos] = (uint32_t)(tbase + (uint64_t)r * S1_THREADS);
+      } else {
+        flag_status(a.status, ST_TIMEOUT);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// (key, insertion code) order; codes are distinct, so it is the stable order.
+template <class K>
+__device__ __forceinline__ bool kv_lt(const K& ka, uint32_t va, const K& kb, uint32_t vb) {
+  return key_lt(ka, kb) || (key_eq(ka, kb) && va < vb);
+}
+
+// Shared-memory slot of bucket entry i: one unused slot after every 16, so
+// that threads reading or writing their own runs of consecutive entries
+// spread over the banks.
+__device__ __forceinline__ uint32_t bk_slot(uint32_t i) { return i + (i >> 4); }
+
 // Sort n <= BK_CAP (key, insertion code) pairs of one bucket in shared
-// memory (bitonic network over pairs ordered by key, then code; codes are
-// distinct, so the order is the stable one) and write them to dst at the
-// same offsets.  src_v == nullptr: the codes are the positions (input
-// dictionary); coherent: src was written earlier in this kernel.
+// memory and write them to dst at the same offsets.  Block merge sort over
+// two shared buffers: the bucket is padded to N = 2^k entries with (max key,
+// max code); thread t owns the I = max(1, N / threads) entries [tI, tI + I),
+// sorts them by insertion, then every round merges neighbouring sorted runs
+// into the other buffer, each thread producing its I outputs after a
+// merge-path search.  Both run heads stay in registers, so an output costs
+// one unconditional load of the next entry.  src_v == nullptr: the codes are
+// the positions (input dictionary); coherent: src was written earlier in
+// this kernel.
 template <int W>
 __device__ void bucket_sort(const typename KeyOf<W>::T* src_k, const uint32_t* src_v, uint64_t off, uint32_t n,
                             bool coherent, typename KeyOf<W>::T* dst_k, uint32_t* dst_v, BucketSmem<W>& S) {
   using K = typename KeyOf<W>::T;
+  constexpr uint32_t R = BK_CAP / S1_THREADS;
   const uint32_t tid = threadIdx.x;
   uint32_t N = 2;
   while (N < n) N <<= 1;
-  for (uint32_t i = tid; i < N; i += S1_THREADS) {
-    if (i < n) {
-      S.keys[i] = coherent ? ldcg_key(src_k + off + i) : load_key(src_k + off + i);
-      S.vals[i] = src_v ? (coherent ? __ldcg(src_v + off + i) : __ldg(src_v + off + i)) : (uint32_t)(off + i);
-    } else {
-      S.keys[i] = key_max_value<K>();
-      S.vals[i] = 0xFFFFFFFFu;
+  const uint32_t I = N > S1_THREADS ? N / S1_THREADS : 1;   // entries per thread
+  const uint32_t T = N / I;                                  // threads with entries
+  {
+    K kr[R];
+    uint32_t vr[R];
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint32_t i = tid + r * S1_THREADS;
+      kr[r] = key_max_value<K>();
+      vr[r] = 0xFFFFFFFFu;
+      if (i < n) {
+        kr[r] = coherent ? ldcg_key(src_k + off + i) : load_key(src_k + off + i);
+        vr[r] = src_v ? (coherent ? __ldcg(src_v + off + i) : __ldg(src_v + off + i)) : (uint32_t)(off + i);
+      }
+    }
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint32_t i = tid + r * S1_THREADS;
+      if (i < N) {
+        S.keys[0][bk_slot(i)] = kr[r];
+        S.vals[0][bk_slot(i)] = vr[r];
+      }
     }
   }
   __syncthreads();
-  for (uint32_t k = 2; k <= N; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = tid; i < (N >> 1); i += S1_THREADS) {
-        const uint32_t lo = 2 * i - (i & (j - 1)), hi = lo + j;
-        const bool up = (lo & k) == 0;
-        const K ka = S.keys[lo], kb = S.keys[hi];
-        const uint32_t va = S.vals[lo], vb = S.vals[hi];
-        const bool gt = key_lt(kb, ka) || (key_eq(ka, kb) && va > vb);
-        if (gt == up) {
-          S.keys[lo] = kb;
-          S.keys[hi] = ka;
-          S.vals[lo] = vb;
-          S.vals[hi] = va;
-        }
+  if (tid < T && I > 1) {
+    K* kk = S.keys[0];
+    uint32_t* vv = S.vals[0];
+    const uint32_t o = tid * I;
+#pragma unroll 1
+    for (uint32_t i = 1; i < I; ++i) {
+      const K x = kk[bk_slot(o + i)];
+      const uint32_t y = vv[bk_slot(o + i)];
+      uint32_t j = i;
+      while (j > 0) {
+        const K z = kk[bk_slot(o + j - 1)];
+        const uint32_t zv = vv[bk_slot(o + j - 1)];
+        if (!kv_lt(x, y, z, zv)) break;
+        kk[bk_slot(o + j)] = z;
+        vv[bk_slot(o + j)] = zv;
+        --j;
       }
-      __syncthreads();
+      kk[bk_slot(o + j)] = x;
+      vv[bk_slot(o + j)] = y;
     }
   }
+  uint32_t cur = 0;
+#pragma unroll 1
+  for (uint32_t w = I; w < N; w <<= 1) {
+    __syncthreads();
+    if (tid < T) {
+      const K* sk = S.keys[cur];
+      const uint32_t* sv = S.vals[cur];
+      K* dk = S.keys[cur ^ 1];
+      uint32_t* dv = S.vals[cur ^ 1];
+      // outputs [tI, tI + I) of the merged run [base, base + 2w)
+      const uint32_t o = tid * I;
+      const uint32_t base = o & ~(2 * w - 1);
+      const uint32_t diag = o - base;
+      const uint32_t a0 = base, b0 = base + w;
+      // entries taken from the first run (ties go to the first run)
+      uint32_t lo = diag > w ? diag - w : 0, hi = diag < w ? diag : w;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint32_t ja = bk_slot(a0 + mid), jb = bk_slot(b0 + diag - 1 - mid);
+        const K xa = sk[ja], xb = sk[jb];
+        const uint32_t va = sv[ja], vb = sv[jb];
+        if (kv_lt(xb, vb, xa, va)) hi = mid;
+        else lo = mid + 1;
+      }
+      uint32_t ia = a0 + lo, ib = b0 + (diag - lo);
+      const uint32_t ea = a0 + w, eb = b0 + w;
+      K ka = sk[bk_slot(min(ia, ea - 1))], kb = sk[bk_slot(min(ib, eb - 1))];
+      uint32_t va = sv[bk_slot(min(ia, ea - 1))], vb = sv[bk_slot(min(ib, eb - 1))];
+#pragma unroll 1
+      for (uint32_t q = 0; q < I; ++q) {
+        const bool takeA = ia < ea && (ib >= eb || !kv_lt(kb, vb, ka, va));
+        dk[bk_slot(o + q)] = takeA ? ka : kb;
+        dv[bk_slot(o + q)] = takeA ? va : vb;
+        ia += takeA;
+        ib += !takeA;
+        const uint32_t nx = bk_slot(takeA ? min(ia, ea - 1) : min(ib, eb - 1));
+        const K kn = sk[nx];
+        const uint32_t vn = sv[nx];
+        ka = takeA ? kn : ka;
+        va = takeA ? vn : va;
+        kb = takeA ? kb : kn;
+        vb = takeA ? vb : vn;
+      }
+    }
+    cur ^= 1;
+  }
+  __syncthreads();
   for (uint32_t i = tid; i < n; i += S1_THREADS) {
-    dst_k[off + i] = S.keys[i];
-    dst_v[off + i] = S.vals[i];
+    dst_k[off + i] = S.keys[cur][bk_slot(i)];
+    dst_v[off + i] = S.vals[cur][bk_slot(i)];
   }
   __syncthreads();
 }
@@ -434,15 +584,33 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   const uint64_t i0 = S.cut[0], i1 = S.cut[1];
   const uint64_t j0 = k0 - i0, j1 = k1 - i1;
   const uint32_t na = (uint32_t)(i1 - i0), nb = (uint32_t)(j1 - j0), nt = na + nb;
-  // one batch of loads: both segments, their perm entries, and the keys just
-  // before the tile (merge predecessor and sortedness check)
-  for (uint32_t x = tid; x < na; x += S1_THREADS) S.keys[x] = load_key(A + i0 + x);
-  for (uint32_t x = tid; x < nb; x += S1_THREADS) {
-    S.keys[na + x] = ld_key(B + j0 + x, bcoh);
-    S.perm[x] = bcoh ? __ldcg(perm + j0 + x) : __ldg(perm + j0 + x);
+  // one batch of loads (all in flight before the first store): both
+  // segments, their perm entries, and the keys just before the tile (merge
+  // predecessor and sortedness check)
+  {
+    constexpr uint32_t R = S1_TILE / S1_THREADS;
+    K kr[R];
+    uint32_t pr[R];
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint32_t x = tid + r * S1_THREADS;
+      if (x < na) {
+        kr[r] = load_key(A + i0 + x);
+      } else if (x < nt) {
+        kr[r] = ld_key(B + j0 + (x - na), bcoh);
+        pr[r] = bcoh ? __ldcg(perm + j0 + (x - na)) : __ldg(perm + j0 + (x - na));
+      }
+    }
+    if (tid == 0 && i0 > 0) S.prevA = load_key(A + i0 - 1);
+    if (tid == 32 && j0 > 0) S.prevB = ld_key(B + j0 - 1, bcoh);
+#pragma unroll
+    for (uint32_t r = 0; r < R; ++r) {
+      const uint32_t x = tid + r * S1_THREADS;
+      if (x < nt) S.keys[x] = kr[r];
+      if (x >= na && x < nt) S.perm[x - na] = pr[r];
+      S.cnt[x] = 0;
+    }
   }
-  if (tid == 0 && i0 > 0) S.prevA = load_key(A + i0 - 1);
-  if (tid == 32 && j0 > 0) S.prevB = ld_key(B + j0 - 1, bcoh);
   __syncthreads();
   const K* sA = S.keys;
   const K* sB = S.keys + na;
@@ -454,64 +622,79 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
     if (!key_lt(prev, sA[x])) flag_status(a.status, ST_UNSORTED);
   }
 
-  // this thread's 8 merged positions: cut inside the tile, then merge
-  const uint32_t kk = tid * S1_ITEMS < nt ? tid * S1_ITEMS : nt;
-  const uint32_t cnt = kk + S1_ITEMS < nt ? S1_ITEMS : nt - kk;
-  uint32_t lo = kk > nb ? kk - nb : 0, hi = kk < na ? kk : na;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (key_le(sA[mid], sB[kk - 1 - mid])) lo = mid + 1;
-    else hi = mid;
-  }
-  uint32_t ia = lo, ib = kk - lo;
-  K key[S1_ITEMS];
-  K last{};
-  uint32_t src[S1_ITEMS];   // bit 31: from U_D; low bits: index inside the tile's segment
-#pragma unroll
-  for (int it = 0; it < (int)S1_ITEMS; ++it) {
-    if ((uint32_t)it < cnt) {
-      const bool takeA = ib >= nb || (ia < na && key_le(sA[ia], sB[ib]));
-      if (takeA) {
-        key[it] = sA[ia];
-        src[it] = ia++;
-      } else {
-        key[it] = sB[ib];
-        src[it] = 0x80000000u | ib++;
+  // Merged order inside the tile (ties: the U_M entry first).  U_D entry j
+  // follows the rank_j = #{i : U_M[i] <= U_D[j]} U_M entries of the tile;
+  // U_M entry i follows the U_D entries with rank <= i.  One fixed-step
+  // binary search per U_D entry, spread over all threads.
+  {
+    const uint32_t top = na ? 1u << (31 - __clz(na)) : 0u;
+    for (uint32_t j = tid; j < nb; j += S1_THREADS) {
+      const K x = sB[j];
+      uint32_t r = 0;
+      for (uint32_t step = top; step > 0; step >>= 1) {
+        const uint32_t p = r + step;
+        const K v = sA[min(p, na) - 1];
+        r = (p <= na && key_le(v, x)) ? p : r;
       }
-      last = key[it];
-    } else {
-      key[it] = K{};
-      src[it] = 0;
+      S.rank[j] = r;
+      if (r < na) atomicAdd(&S.cnt[r], 1u);
     }
   }
-  if (cnt > 0) S.last[tid] = last;
   __syncthreads();
 
-  // duplicates: equal to the previous key in merged order
-  uint32_t dupmask = 0, nondup = 0;
+  // duplicates: a U_D entry equal to the key before it in merged order (a
+  // U_M entry never is: U_M increases and ties put it first)
+  K kp{};
+  if (i0 > 0 && j0 > 0) kp = key_max(S.prevA, S.prevB);   // the key at merged position k0 - 1
+  else if (i0 > 0) kp = S.prevA;
+  else if (j0 > 0) kp = S.prevB;
+  auto nondup_at = [&](uint32_t j) -> uint32_t {
+    if (j >= nb) return 0u;
+    const uint32_t r = S.rank[j];
+    bool has_prev = true;
+    K pk;
+    if (j > 0 && S.rank[j - 1] == r) pk = sB[j - 1];
+    else if (r > 0) pk = sA[r - 1];
+    else {
+      pk = kp;
+      has_prev = k0 > 0;
+    }
+    return has_prev && key_eq(sB[j], pk) ? 0u : 1u;
+  };
+  // U_D entries placed before this thread's U_M entries [8t, 8t + 8)
+  uint32_t cinc[8];
   {
-    bool has_prev = tid > 0 ? true : k0 > 0;
-    K prev;
-    if (tid > 0) {
-      prev = S.last[tid - 1];
-    } else if (i0 > 0 && j0 > 0) {
-      prev = key_max(S.prevA, S.prevB);   // the key at merged position k0 - 1
-    } else {
-      prev = i0 > 0 ? S.prevA : S.prevB;
-    }
-#pragma unroll
-    for (int it = 0; it < (int)S1_ITEMS; ++it) {
-      if ((uint32_t)it < cnt) {
-        const bool dup = has_prev && key_eq(key[it], prev);
-        dupmask |= (uint32_t)dup << it;
-        nondup += !dup;
-        prev = key[it];
-        has_prev = true;
-      }
-    }
+    const uint4 c0 = reinterpret_cast<const uint4*>(S.cnt)[2 * tid];
+    const uint4 c1 = reinterpret_cast<const uint4*>(S.cnt)[2 * tid + 1];
+    cinc[0] = c0.x;
+    cinc[1] = cinc[0] + c0.y;
+    cinc[2] = cinc[1] + c0.z;
+    cinc[3] = cinc[2] + c0.w;
+    cinc[4] = cinc[3] + c1.x;
+    cinc[5] = cinc[4] + c1.y;
+    cinc[6] = cinc[5] + c1.z;
+    cinc[7] = cinc[6] + c1.w;
   }
-  uint32_t ttotal = 0;
-  const uint32_t texcl = block_excl_scan(nondup, S.wsum, &ttotal);
+  // the U_M prefix and the first round of U_D non-duplicates in one block
+  // scan (each total is at most 2048: 16 bits), further rounds alone
+  uint32_t total = 0;
+  const uint32_t pex = block_excl_scan((nondup_at(tid) << 16) | cinc[7], S.wsum, &total);
+  {
+    const uint32_t cx = pex & 0xFFFFu;
+    reinterpret_cast<uint4*>(S.cnt)[2 * tid] = make_uint4(cx + cinc[0], cx + cinc[1], cx + cinc[2], cx + cinc[3]);
+    reinterpret_cast<uint4*>(S.cnt)[2 * tid + 1] = make_uint4(cx + cinc[4], cx + cinc[5], cx + cinc[6], cx + cinc[7]);
+  }
+  if (tid < nb) S.ndx[tid] = pex >> 16;
+  uint32_t ndB = total >> 16;
+  for (uint32_t q = 1; q * S1_THREADS < nb; ++q) {
+    const uint32_t j = q * S1_THREADS + tid;
+    uint32_t tq = 0;
+    const uint32_t e = block_excl_scan(nondup_at(j), S.wsum, &tq);
+    if (j < nb) S.ndx[j] = ndB + e;
+    ndB += tq;
+  }
+  if (tid == 0) S.ndx[nb] = ndB;
+  const uint32_t ttotal = na + ndB;
 
   // decoupled look-back: the whole block reads 256 predecessors per round
   // trip and sums them down to the nearest inclusive prefix
@@ -560,32 +743,37 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   }
   __syncthreads();
 
-  // codes and writes
-  uint64_t c = S.excl + texcl;
+  // codes and writes.  U_M entry i: code = excl + i + (non-duplicate U_D
+  // entries before it); U_D entry j: code = excl + rank_j + (non-duplicate
+  // U_D entries before it), minus one for a duplicate (the code of the
+  // equal key before it).  U' and X_M go out in U_M order (consecutive
+  // threads, nearly consecutive codes); X_D is scattered through perm.
+  const uint64_t excl = S.excl;
   K* unew = static_cast<K*>(a.unew);
-#pragma unroll
-  for (int it = 0; it < (int)S1_ITEMS; ++it) {
-    if ((uint32_t)it < cnt) {
-      const bool dup = (dupmask >> it) & 1u;
-      c += !dup;
-      const uint64_t code = c - 1;
-      if (code >= n) {
-        flag_status(a.status, ST_TIMEOUT);
-        continue;
-      }
-      if (!dup) unew[code] = key[it];
-      const uint32_t s = src[it];
-      if (s & 0x80000000u) {
-        const uint32_t pj = S.perm[s & 0x7FFFFFFFu];
-        if (pj < d) a.xd[pj] = (uint32_t)code;
-        else flag_status(a.status, ST_CODE);
-      } else {
-        a.xm[i0 + s] = (uint32_t)code;
-      }
+  for (uint32_t x = tid; x < na; x += S1_THREADS) {
+    const uint64_t code = excl + x + S.ndx[S.cnt[x]];
+    if (code < n) {
+      unew[code] = sA[x];
+      a.xm[i0 + x] = (uint32_t)code;
+    } else {
+      flag_status(a.status, ST_TIMEOUT);
     }
   }
+  for (uint32_t j = tid; j < nb; j += S1_THREADS) {
+    const uint32_t before = S.ndx[j];
+    const bool nondup = S.ndx[j + 1] != before;
+    const uint64_t code = excl + S.rank[j] + before - (nondup ? 0u : 1u);
+    if (code >= n) {
+      flag_status(a.status, ST_TIMEOUT);
+      continue;
+    }
+    if (nondup) unew[code] = sB[j];
+    const uint32_t pj = S.perm[j];
+    if (pj < d) a.xd[pj] = (uint32_t)code;
+    else flag_status(a.status, ST_CODE);
+  }
   if (tile == a.merge_tiles - 1 && tid == 0) {
-    const uint64_t u = S.excl + ttotal;
+    const uint64_t u = excl + ttotal;
     *a.d_u = u;
     *a.d_bits = bits_for(u);
   }
@@ -594,13 +782,21 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
 
 // ---------------------------------------------------------------- the kernel
 template <int W>
-__global__ void __launch_bounds__(S1_THREADS) step1_kernel(Step1Args a) {
+__global__ void __launch_bounds__(S1_THREADS, W == 16 ? 2 : 3) step1_kernel(Step1Args a) {
   using K = typename KeyOf<W>::T;
   extern __shared__ __align__(16) unsigned char dsmem[];
   Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
   uint32_t* s_plan = reinterpret_cast<uint32_t*>(dsmem + (sizeof(Step1Smem<W>) + 15) / 16 * 16);
   uint32_t* s_wsum = s_plan + W * 256;
 
+  // U_M is first read by the merge's co-rank searches (dependent loads):
+  // start pulling it into L2 while the delta dictionary is sorted
+  if ((a.phases & S1_SORT) && (a.phases & S1_MERGE) && a.m > 0 && a.d > BK_SINGLE) {
+    const char* base = static_cast<const char*>(a.a);
+    const uint64_t lines = (a.m * W + 127) / 128;
+    for (uint64_t l = (uint64_t)blockIdx.x * S1_THREADS + threadIdx.x; l < lines; l += (uint64_t)gridDim.x * S1_THREADS)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + l * 128));
+  }
   uint32_t nbar = 0;
   const K* ud = static_cast<const K*>(a.b);
   const uint32_t* up = a.perm;
@@ -622,7 +818,7 @@ __global__ void __launch_bounds__(S1_THREADS) step1_kernel(Step1Args a) {
         // one stable pass on the top varying digit, then each of its 256
         // buckets sorted in shared memory in place
         const int top = 31 - __clz(run);
-        for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) pass_tile<W>(a, top, t, 0, s_plan, U.s);
+        for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) msd_tile<W>(a, top, t, s_plan, U.s);
         grid_barrier(a.barriers, nbar++, a.status);
         for (uint32_t b = blockIdx.x; b < 256; b += gridDim.x) {
           const uint32_t off = s_plan[top * 256 + b];
@@ -721,7 +917,8 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
   uint64_t cap = (uint64_t)per_sm * sm_count;
   if (a.grid_cap && a.grid_cap < cap) cap = a.grid_cap;
   const uint32_t grid = (uint32_t)std::min(want, cap);
-  a.hist_blocks = (uint32_t)std::min<uint64_t>(grid, std::max<uint64_t>(1, (a.d + 4095) / 4096));
+  a.hist_blocks = (uint32_t)std::min<uint64_t>(
+      grid, std::max<uint64_t>(1, (a.d + S1_THREADS * HI_ITEMS - 1) / (S1_THREADS * HI_ITEMS)));
 
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
