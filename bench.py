@@ -125,6 +125,19 @@ class ClockSampler:
         except (OSError, FileNotFoundError):
             self.proc = None
 
+    def wait_ready(self, timeout: float = 1.0):
+        """Wait for the first sample (or the timeout): nvidia-smi's start-up
+        stalls the GPU for about a millisecond, which must not land in a
+        timed region."""
+        if self.proc is None:
+            return
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < timeout:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
+        time.sleep(0.05)
+
     def stop(self):
         if self.proc is None:
             return None
@@ -246,9 +259,14 @@ def run_gpu(args):
         if world > 1:
             torch.distributed.barrier()
 
-    # warm-up (also checks the result once against the status word)
+    # clock samples run from before the warm-up to after the timed region
+    sampler = ClockSampler(local, not args.no_clocks)
+    sampler.wait_ready()
+    # warm-up with the timed loop's flags (the first timed call would
+    # otherwise create the context's event ring; also checks the result once
+    # against the status word)
     for _ in range(max(args.warmup, 3)):
-        dm.dm_merge_column(ctx, cin, cout, stream)
+        dm.dm_merge_column(ctx, cin, cout, stream, dm.DM_FLAG_TIMING)
     torch.cuda.synchronize()
     st = ctx.sync_status()
     if st != dm.DM_OK:
@@ -256,7 +274,6 @@ def run_gpu(args):
     u, b_new = res.u_bits()
 
     # timed region: K whole merges, CUDA events on the launching stream
-    sampler = ClockSampler(local, not args.no_clocks)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     launches0 = ctx.launches
     ctx.timing_sum()
@@ -436,6 +453,7 @@ def run_table(args):
 
     launches0 = ctx.launches
     sampler = ClockSampler(local, not args.no_clocks)
+    sampler.wait_ready()
     t_batched, per_b = timed(0)
     clocks = sampler.stop()
     launches = (ctx.launches - launches0) // (args.steps + max(args.warmup, 3))
@@ -513,6 +531,7 @@ def run_serve(args):
     tabs = rng.integers(0, cfg["ntables"], nreq)
     gaps = rng.exponential(1.0 / cfg["rate"], nreq) if cfg["rate"] > 0 else np.zeros(nreq)
     sampler = ClockSampler(local, not args.no_clocks)
+    sampler.wait_ready()
     t0 = time.perf_counter()
     due = t0
     for t, g in zip(tabs, gaps):

@@ -9,7 +9,11 @@ namespace dm {
 // ---------------------------------------------------------------- Step 1
 constexpr int RS_ITEMS = 4;       // keys per thread of a sort tile
 constexpr int RS_TILE = 256 * RS_ITEMS;   // keys per sort tile
-constexpr int MG_TILE = 2048;     // merged positions per merge tile
+// Merged positions per merge tile: 4096 for 4- and 8-byte keys (a 100M-row
+// column's merge fits one wave of tiles), 2048 for 16-byte keys (shared
+// memory); MG_TILE_MIN bounds the tile count for any width.
+constexpr uint32_t mg_tile(uint32_t w) { return w == 16 ? 2048u : 4096u; }
+constexpr uint32_t MG_TILE_MIN = 2048;
 constexpr uint32_t S1_SORT = 1, S1_MERGE = 2, S1_DIR = 4;   // phases
 constexpr uint32_t S1_BARRIERS = 32;                        // barrier counters per launch
 
@@ -53,7 +57,7 @@ cudaError_t step1_prepare();
 uint32_t step1_capacity(uint32_t w, uint32_t sm_count);
 
 uint32_t sort_tiles(uint64_t d);
-uint32_t merge_tiles(uint64_t n);
+uint32_t merge_tiles(uint64_t n, uint32_t w);
 // 32-bit words of bookkeeping to zero before a Step 1 launch that merges
 // n_merge dictionary entries and sorts d_sort keys of w bytes.
 uint64_t step1_zeroed_words(uint32_t w, uint64_t n_merge, uint64_t d_sort);

@@ -46,11 +46,10 @@ namespace {
 
 constexpr uint32_t S1_THREADS = 256;
 constexpr uint32_t S1_WARPS = S1_THREADS / 32;
-constexpr uint32_t S1_ITEMS = 8;                      // merge positions per thread
-constexpr uint32_t S1_TILE = S1_THREADS * S1_ITEMS;   // 2048 merged positions per merge tile
 constexpr uint32_t SR_ITEMS = RS_ITEMS;               // sort keys per thread
 constexpr uint32_t SR_TILE = S1_THREADS * SR_ITEMS;   // sort keys per sort tile
-static_assert(S1_TILE == MG_TILE && SR_TILE == RS_TILE, "tile sizes");
+static_assert(SR_TILE == RS_TILE, "tile sizes");
+static_assert(mg_tile(4) % (4 * S1_THREADS) == 0 && mg_tile(16) % (4 * S1_THREADS) == 0, "merge tiles");
 
 // ---------------------------------------------------------------- loads
 template <class K>
@@ -104,11 +103,12 @@ struct SortSmem {
 template <int W>
 struct MergeSmem {
   using K = typename KeyOf<W>::T;
-  K keys[S1_TILE];                 // U_M segment then U_D segment
-  uint32_t perm[S1_TILE];          // insertion codes of the U_D segment
-  uint32_t rank[S1_TILE];          // per U_D entry: U_M entries of the tile at or below it
-  alignas(16) uint32_t cnt[S1_TILE];   // per U_M entry: U_D entries placed right before it, then the prefix
-  uint32_t ndx[S1_TILE + 1];       // per U_D entry: non-duplicate U_D entries before it (and the total)
+  static constexpr uint32_t T = mg_tile(W);
+  K keys[T];                       // U_M segment then U_D segment
+  uint32_t perm[T];                // insertion codes of the U_D segment
+  uint32_t rank[T];                // per U_D entry: U_M entries of the tile at or below it
+  alignas(16) uint32_t cnt[T];     // per U_M entry: U_D entries placed right before it, then the prefix
+  uint32_t ndx[T + 1];             // per U_D entry: non-duplicate U_D entries before it (and the total)
   uint32_t wsum[S1_WARPS];
   uint64_t cut[2];
   uint64_t excl, lb_sum;
@@ -124,7 +124,10 @@ struct BucketSmem {
   using K = typename KeyOf<W>::T;
   K keys[2][BK_CAP + BK_CAP / 16];   // ping-pong buffers of the merge rounds (bk_slot layout)
   uint32_t vals[2][BK_CAP + BK_CAP / 16];
+  uint32_t cnt[256];                 // sub-bucket counts, then cursors
+  uint32_t wsum[S1_WARPS];
 };
+constexpr uint32_t BK_SUB_MAX = 32;   // largest sub-bucket one thread sorts by insertion
 
 template <int W>
 union Step1Smem {
@@ -195,27 +198,35 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* wsum, 
   return excl;
 }
 
-// The sort plan from the global histogram: first slot of every digit of
-// every pass, and the mask of passes that run (a pass whose digit is the
-// same for every key is skipped; if none remains, the last pass runs so the
-// result always lands in a ping-pong buffer).  Every block computes it.
+// The sort plan from the global histogram, computed by every block: the
+// mask of bytes whose digit varies (a byte whose digit is the same for every
+// key is skipped; if none varies, the last one runs so the result always
+// lands in a ping-pong buffer), and the first slot of every digit of the
+// bytes that will be passed over.
 //
 // It also decides between the two ways to finish the sort: when every bucket
-// of the most significant digit that varies holds at most BK_CAP keys, one
-// stable pass on that digit plus one sort of each bucket in shared memory
-// (*msd = true); otherwise all running passes, least significant first.
+// of the most significant byte that varies holds at most BK_CAP keys, one
+// partition on that byte plus one sort of each bucket in shared memory
+// (*msd = true; only that byte's slots are computed); otherwise all varying
+// bytes, least significant first.
 template <int W>
 __device__ uint32_t plan_phase(const Step1Args& a, uint32_t* s_plan, uint32_t* wsum, bool* msd) {
-  const uint32_t t = threadIdx.x;
+  const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
   uint32_t v[W];
 #pragma unroll
   for (int p = 0; p < W; ++p) v[p] = ld_volatile(&a.hist[p * 256 + t]);
-  uint32_t run = 0;
+  // bytes whose digit is the same for every key: one vote for all bytes
+  uint32_t cmask = 0;
 #pragma unroll
-  for (int p = 0; p < W; ++p) {
-    if (!__syncthreads_or((uint64_t)v[p] == a.d)) run |= 1u << p;
-    s_plan[p * 256 + t] = block_excl_scan(v[p], wsum, nullptr);
-  }
+  for (int p = 0; p < W; ++p) cmask |= ((uint64_t)v[p] == a.d ? 1u : 0u) << p;
+  cmask = __reduce_or_sync(0xFFFFFFFFu, cmask);
+  if (lane == 0) wsum[warp] = cmask;
+  __syncthreads();
+  cmask = 0;
+#pragma unroll
+  for (uint32_t w = 0; w < S1_WARPS; ++w) cmask |= wsum[w];
+  __syncthreads();
+  uint32_t run = ~cmask & ((1u << W) - 1u);
   run = run ? run : (1u << (W - 1));
   const int top = 31 - __clz(run);
   uint32_t vtop = 0;
@@ -223,6 +234,14 @@ __device__ uint32_t plan_phase(const Step1Args& a, uint32_t* s_plan, uint32_t* w
   for (int p = 0; p < W; ++p)
     if (p == top) vtop = v[p];
   *msd = !__syncthreads_or(vtop > BK_CAP);
+  if (*msd) {
+    s_plan[top * 256 + t] = block_excl_scan(vtop, wsum, nullptr);
+  } else {
+#pragma unroll
+    for (int p = 0; p < W; ++p)
+      if ((run >> p) & 1u) s_plan[p * 256 + t] = block_excl_scan(v[p], wsum, nullptr);
+  }
+  __syncthreads();
   return run;
 }
 
@@ -542,6 +561,86 @@ __device__ void bucket_sort(const typename KeyOf<W>::T* src_k, const uint32_t* s
   __syncthreads();
 }
 
+// Sort one bucket (as bucket_sort) by one more counting-sort level: the
+// keys are counted and scattered on byte `sub` (the next byte below the
+// bucket's that varies) into 256 sub-buckets, and each thread sorts one
+// sub-bucket by insertion on (key, insertion code).  A bucket with a
+// sub-bucket above BK_SUB_MAX keys goes to the merge sort instead.
+template <int W>
+__device__ void bucket_sort_sub(const typename KeyOf<W>::T* src_k, const uint32_t* src_v, uint64_t off, uint32_t n,
+                                bool coherent, typename KeyOf<W>::T* dst_k, uint32_t* dst_v, int sub,
+                                BucketSmem<W>& S) {
+  using K = typename KeyOf<W>::T;
+  constexpr uint32_t R = BK_CAP / S1_THREADS;
+  const uint32_t tid = threadIdx.x;
+  K kr[R];
+  uint32_t vr[R], dg[R];
+  S.cnt[tid] = 0;
+#pragma unroll
+  for (uint32_t r = 0; r < R; ++r) {
+    const uint32_t i = tid + r * S1_THREADS;
+    dg[r] = 256;
+    if (i < n) {
+      kr[r] = coherent ? ldcg_key(src_k + off + i) : load_key(src_k + off + i);
+      vr[r] = src_v ? (coherent ? __ldcg(src_v + off + i) : __ldg(src_v + off + i)) : (uint32_t)(off + i);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (uint32_t r = 0; r < R; ++r) {
+    if (tid + r * S1_THREADS < n) {
+      dg[r] = key_digit(kr[r], sub);
+      atomicAdd(&S.cnt[dg[r]], 1u);
+    }
+  }
+  __syncthreads();
+  const uint32_t c = S.cnt[tid];
+  if (__syncthreads_or(c > BK_SUB_MAX)) {
+    bucket_sort<W>(src_k, src_v, off, n, coherent, dst_k, dst_v, S);
+    return;
+  }
+  uint32_t total = 0;
+  const uint32_t st = block_excl_scan(c, S.wsum, &total);
+  S.cnt[tid] = st;   // cursor of sub-bucket tid
+  __syncthreads();
+  K* kk = S.keys[0];
+  uint32_t* vv = S.vals[0];
+#pragma unroll
+  for (uint32_t r = 0; r < R; ++r) {
+    if (dg[r] < 256) {
+      const uint32_t pos = atomicAdd(&S.cnt[dg[r]], 1u);
+      if (pos < BK_CAP) {
+        kk[pos] = kr[r];
+        vv[pos] = vr[r];
+      }
+    }
+  }
+  __syncthreads();
+  // sub-bucket tid: entries [st, st + c)
+#pragma unroll 1
+  for (uint32_t i = 1; i < c; ++i) {
+    const K x = kk[st + i];
+    const uint32_t y = vv[st + i];
+    uint32_t j = i;
+    while (j > 0) {
+      const K z = kk[st + j - 1];
+      const uint32_t zv = vv[st + j - 1];
+      if (!kv_lt(x, y, z, zv)) break;
+      kk[st + j] = z;
+      vv[st + j] = zv;
+      --j;
+    }
+    kk[st + j] = x;
+    vv[st + j] = y;
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < n; i += S1_THREADS) {
+    dst_k[off + i] = kk[i];
+    dst_v[off + i] = vv[i];
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- Step 1(b)
 // Number of U_M entries among the first k merged positions (ties: U_M
 // first).  Whole warp; 32 probes per round narrow the range 33-fold.
@@ -574,8 +673,10 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   const K* A = static_cast<const K*>(a.a);
   const uint64_t m = a.m, d = a.d, n = m + d;
 
-  const uint64_t k0 = (uint64_t)tile * S1_TILE;
-  const uint64_t k1 = k0 + S1_TILE < n ? k0 + S1_TILE : n;
+  constexpr uint32_t T = MergeSmem<W>::T;   // merged positions per tile
+  constexpr uint32_t E = T / S1_THREADS;     // U_M prefix entries per thread
+  const uint64_t k0 = (uint64_t)tile * T;
+  const uint64_t k1 = k0 + T < n ? k0 + T : n;
   if (warp < 2) {
     const uint64_t c = corank_warp(A, m, B, d, warp == 0 ? k0 : k1, bcoh);
     if (lane == 0) S.cut[warp] = c;
@@ -588,7 +689,7 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   // segments, their perm entries, and the keys just before the tile (merge
   // predecessor and sortedness check)
   {
-    constexpr uint32_t R = S1_TILE / S1_THREADS;
+    constexpr uint32_t R = T / S1_THREADS;
     K kr[R];
     uint32_t pr[R];
 #pragma unroll
@@ -661,28 +762,29 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
     }
     return has_prev && key_eq(sB[j], pk) ? 0u : 1u;
   };
-  // U_D entries placed before this thread's U_M entries [8t, 8t + 8)
-  uint32_t cinc[8];
+  // U_D entries placed before this thread's U_M entries [Et, Et + E)
+  uint32_t cinc[E];
   {
-    const uint4 c0 = reinterpret_cast<const uint4*>(S.cnt)[2 * tid];
-    const uint4 c1 = reinterpret_cast<const uint4*>(S.cnt)[2 * tid + 1];
-    cinc[0] = c0.x;
-    cinc[1] = cinc[0] + c0.y;
-    cinc[2] = cinc[1] + c0.z;
-    cinc[3] = cinc[2] + c0.w;
-    cinc[4] = cinc[3] + c1.x;
-    cinc[5] = cinc[4] + c1.y;
-    cinc[6] = cinc[5] + c1.z;
-    cinc[7] = cinc[6] + c1.w;
+    uint32_t run = 0;
+#pragma unroll
+    for (uint32_t v = 0; v < E / 4; ++v) {
+      const uint4 c = reinterpret_cast<const uint4*>(S.cnt)[(E / 4) * tid + v];
+      cinc[4 * v] = run += c.x;
+      cinc[4 * v + 1] = run += c.y;
+      cinc[4 * v + 2] = run += c.z;
+      cinc[4 * v + 3] = run += c.w;
+    }
   }
   // the U_M prefix and the first round of U_D non-duplicates in one block
-  // scan (each total is at most 2048: 16 bits), further rounds alone
+  // scan (each total is at most 4096: 16 bits), further rounds alone
   uint32_t total = 0;
-  const uint32_t pex = block_excl_scan((nondup_at(tid) << 16) | cinc[7], S.wsum, &total);
+  const uint32_t pex = block_excl_scan((nondup_at(tid) << 16) | cinc[E - 1], S.wsum, &total);
   {
     const uint32_t cx = pex & 0xFFFFu;
-    reinterpret_cast<uint4*>(S.cnt)[2 * tid] = make_uint4(cx + cinc[0], cx + cinc[1], cx + cinc[2], cx + cinc[3]);
-    reinterpret_cast<uint4*>(S.cnt)[2 * tid + 1] = make_uint4(cx + cinc[4], cx + cinc[5], cx + cinc[6], cx + cinc[7]);
+#pragma unroll
+    for (uint32_t v = 0; v < E / 4; ++v)
+      reinterpret_cast<uint4*>(S.cnt)[(E / 4) * tid + v] =
+          make_uint4(cx + cinc[4 * v], cx + cinc[4 * v + 1], cx + cinc[4 * v + 2], cx + cinc[4 * v + 3]);
   }
   if (tid < nb) S.ndx[tid] = pex >> 16;
   uint32_t ndB = total >> 16;
@@ -782,21 +884,13 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
 
 // ---------------------------------------------------------------- the kernel
 template <int W>
-__global__ void __launch_bounds__(S1_THREADS, W == 16 ? 2 : 3) step1_kernel(Step1Args a) {
+__global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
   using K = typename KeyOf<W>::T;
   extern __shared__ __align__(16) unsigned char dsmem[];
   Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
   uint32_t* s_plan = reinterpret_cast<uint32_t*>(dsmem + (sizeof(Step1Smem<W>) + 15) / 16 * 16);
   uint32_t* s_wsum = s_plan + W * 256;
 
-  // U_M is first read by the merge's co-rank searches (dependent loads):
-  // start pulling it into L2 while the delta dictionary is sorted
-  if ((a.phases & S1_SORT) && (a.phases & S1_MERGE) && a.m > 0 && a.d > BK_SINGLE) {
-    const char* base = static_cast<const char*>(a.a);
-    const uint64_t lines = (a.m * W + 127) / 128;
-    for (uint64_t l = (uint64_t)blockIdx.x * S1_THREADS + threadIdx.x; l < lines; l += (uint64_t)gridDim.x * S1_THREADS)
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(base + l * 128));
-  }
   uint32_t nbar = 0;
   const K* ud = static_cast<const K*>(a.b);
   const uint32_t* up = a.perm;
@@ -820,10 +914,15 @@ __global__ void __launch_bounds__(S1_THREADS, W == 16 ? 2 : 3) step1_kernel(Step
         const int top = 31 - __clz(run);
         for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) msd_tile<W>(a, top, t, s_plan, U.s);
         grid_barrier(a.barriers, nbar++, a.status);
+        // the next byte below the top one that varies splits each bucket once more
+        const uint32_t lower = run & ((1u << top) - 1u);
+        const int sub = lower ? 31 - __clz(lower) : -1;
         for (uint32_t b = blockIdx.x; b < 256; b += gridDim.x) {
           const uint32_t off = s_plan[top * 256 + b];
           const uint32_t n = (b < 255 ? s_plan[top * 256 + b + 1] : (uint32_t)a.d) - off;
-          if (n > 1) bucket_sort<W>(k0, v0, off, n, true, k0, v0, U.b);
+          if (n <= 1) continue;
+          if (sub >= 0) bucket_sort_sub<W>(k0, v0, off, n, true, k0, v0, sub, U.b);
+          else bucket_sort<W>(k0, v0, off, n, true, k0, v0, U.b);
         }
         ud = k0;
         up = v0;
@@ -953,16 +1052,16 @@ uint32_t step1_capacity(uint32_t w, uint32_t sm_count) {
 }
 
 uint32_t sort_tiles(uint64_t d) { return (uint32_t)((d + RS_TILE - 1) / RS_TILE); }
-uint32_t merge_tiles(uint64_t n) { return (uint32_t)((n + MG_TILE - 1) / MG_TILE); }
+uint32_t merge_tiles(uint64_t n, uint32_t w) { return (uint32_t)((n + mg_tile(w) - 1) / mg_tile(w)); }
 
 uint64_t step1_zeroed_words(uint32_t w, uint64_t n_merge, uint64_t d) {
   // merge look-back (64-bit words), barrier counters, digit histograms,
   // sort look-back
-  return 2ull * merge_tiles(n_merge) + S1_BARRIERS + (d ? (uint64_t)w * 256 + (uint64_t)w * sort_tiles(d) * 256 : 0);
+  return 2ull * merge_tiles(n_merge, w) + S1_BARRIERS + (d ? (uint64_t)w * 256 + (uint64_t)w * sort_tiles(d) * 256 : 0);
 }
 
 void step1_layout(uint32_t w, uint64_t n_merge, uint64_t d, uint32_t* zero, Step1Args* a) {
-  const uint32_t mt = merge_tiles(n_merge);
+  const uint32_t mt = merge_tiles(n_merge, w);
   a->merge_lb = reinterpret_cast<uint64_t*>(zero);
   a->merge_tiles = mt;
   a->barriers = zero + 2ull * mt;
@@ -1006,7 +1105,7 @@ cudaError_t launch_sort_copy_out(uint32_t w, void** final_slot, uint64_t d, void
 // host it only names a shadow), so the device address is looked up once per
 // device with cudaGetSymbolAddress.
 namespace {
-constexpr uint32_t kNoAllocTiles = (DM_NOALLOC_MAX_ENTRIES + dm::MG_TILE - 1) / dm::MG_TILE;
+constexpr uint32_t kNoAllocTiles = (DM_NOALLOC_MAX_ENTRIES + dm::MG_TILE_MIN - 1) / dm::MG_TILE_MIN;
 static __device__ __align__(256) uint64_t g_noalloc_scratch[kNoAllocTiles + dm::S1_BARRIERS / 2];
 
 constexpr int kMaxDevices = 64;

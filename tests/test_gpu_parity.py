@@ -78,11 +78,38 @@ def test_sort_constant_digits(ctx, w):
         assert np.array_equal(dm.to_host(perm, np.uint32), perm_ref)
 
 
+@pytest.mark.parametrize("w", [4, 8, 16])
+@pytest.mark.parametrize("lowbits", [1, 6, 12])
+def test_sort_skewed_lower_bytes(ctx, w, lowbits):
+    """A uniform top byte over few values in the lowest byte(s): the buckets split on
+    a low-entropy byte (crowded sub-buckets take the merge sort), with many repeats."""
+    import torch
+    rng = np.random.default_rng(100 + w + lowbits)
+    d = 120_000
+    if w == 16:
+        dd = np.zeros((d, 2), np.uint64)
+        dd[:, 0] = rng.integers(0, 256, d).astype(np.uint64) << np.uint64(56)
+        dd[:, 1] = rng.integers(0, 1 << lowbits, d).astype(np.uint64)
+    else:
+        t = kd(w)
+        top = rng.integers(0, 256, d).astype(t) << t(8 * w - 8)
+        dd = top | rng.integers(0, 1 << lowbits, d).astype(t)
+    ud_ref, perm_ref = oracle.sort_delta(w, dd)
+    ud = dm.key_tensor_empty(d, w)
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    dm.dm_sort_delta(ctx, w, dm.to_device(dd), d, ud, perm)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_OK
+    assert np.array_equal(dm.to_host(ud, kd(w)), ud_ref)
+    assert np.array_equal(dm.to_host(perm, np.uint32), perm_ref)
+
+
 # ------------------------------------------------------------------ Step 1(b) + 2(a)
 
 @pytest.mark.parametrize("w", [4, 8, 16])
-@pytest.mark.parametrize("m,d", [(0, 5), (5, 0), (1, 1), (2048, 1), (3000, 5000), (100_000, 9_000),
-                                 (7, 70_000), (250_000, 250_000)])
+@pytest.mark.parametrize("m,d", [(0, 5), (5, 0), (1, 1), (2048, 1), (3000, 5000), (4095, 1), (4096, 1),
+                                 (4097, 4096), (100_000, 9_000), (7, 70_000), (250_000, 250_000),
+                                 (1_500_000, 200_001)])
 def test_merge_dicts_parity(ctx, w, m, d):
     import torch
     um = synth.dictionary(synth.subseed(m, 1), w, m)
