@@ -22,7 +22,9 @@
 //   * packed rows go to a double-buffered shared tile that one bulk copy
 //     stores to global memory; the last tile is stored with clipped plain
 //     stores and zero padding up to the stream's 16-byte end.
-// Tiles that hold delta rows or the main/delta boundary use a plain path.
+// Tiles of delta rows only read their codes with wide loads and map them
+// through X_D; the tile at the main/delta boundary and a ragged last tile
+// use a plain per-code path.
 #include <string.h>
 
 #include <mutex>
@@ -290,28 +292,84 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArg
 #pragma unroll
         for (int j = 0; j < 32; ++j) x[j] = __ldg(a.xm + c[j]);
       }
-    } else {
-      const uint64_t i0 = t * RE_TILE + lane * 32;
+    } else if (t * RE_TILE >= a.n_main && (t + 1) * RE_TILE <= n_out) {
+      // a tile of delta rows only: 32 consecutive delta codes per lane
+      // (16-byte loads when aligned), range-checked, mapped through X_D
+      const uint32_t* src = a.dcodes + (t * RE_TILE - a.n_main) + lane * 32;
+      uint32_t c[32];
+      if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const uint64_t i = i0 + j;
-        uint32_t v = 0;
-        if (i < a.n_main) {
-          uint32_t cc = code_at(a.main_words, a.main_words_n, i, B);
+        for (int q = 0; q < 8; ++q) {
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(src) + q);
+          c[4 * q] = v.x;
+          c[4 * q + 1] = v.y;
+          c[4 * q + 2] = v.z;
+          c[4 * q + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) c[j] = __ldg(src + j);
+      }
+      uint32_t mx = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) mx = max(mx, c[j]);
+      if (__any_sync(0xFFFFFFFFu, mx >= a.d)) {
+        if (mx >= a.d) flag_status(a.status, ST_CODE);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) c[j] = min(c[j], a.d - 1);
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = __ldg(a.xd + c[j]);
+    } else {
+      // the main/delta boundary tile and a ragged last tile, per code: a
+      // lane's codes are all main rows, all delta rows (or past the end),
+      // or (one lane at most) mixed; the first two classes load without
+      // per-code branches, so their loads are in flight together
+      const uint64_t i0 = t * RE_TILE + lane * 32;
+      if (i0 + 32 <= a.n_main) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          uint32_t cc = code_at(a.main_words, a.main_words_n, i0 + j, B);
           if (cc >= a.m) {
             flag_status(a.status, ST_CODE);
             cc = a.m - 1;
           }
-          v = __ldg(a.xm + cc);
-        } else if (i < n_out) {
-          uint32_t cc = __ldg(a.dcodes + (i - a.n_main));
-          if (cc >= a.d) {
+          x[j] = __ldg(a.xm + cc);
+        }
+      } else if (i0 >= a.n_main) {
+        const uint64_t nd = a.n_delta;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const uint64_t r = i0 + j - a.n_main;
+          uint32_t cc = r < nd ? __ldg(a.dcodes + r) : 0u;
+          if (r < nd && cc >= a.d) {
             flag_status(a.status, ST_CODE);
             cc = a.d - 1;
           }
-          v = __ldg(a.xd + cc);
+          x[j] = r < nd ? __ldg(a.xd + cc) : 0u;
         }
-        x[j] = v;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const uint64_t i = i0 + j;
+          uint32_t v = 0;
+          if (i < a.n_main) {
+            uint32_t cc = code_at(a.main_words, a.main_words_n, i, B);
+            if (cc >= a.m) {
+              flag_status(a.status, ST_CODE);
+              cc = a.m - 1;
+            }
+            v = __ldg(a.xm + cc);
+          } else if (i < n_out) {
+            uint32_t cc = __ldg(a.dcodes + (i - a.n_main));
+            if (cc >= a.d) {
+              flag_status(a.status, ST_CODE);
+              cc = a.d - 1;
+            }
+            v = __ldg(a.xd + cc);
+          }
+          x[j] = v;
+        }
       }
     }
 
