@@ -169,6 +169,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
+    committed ncu record under profiles/, or None when there is none or the
+    kernel's sources changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+    except (OSError, ValueError, KeyError):
+        return None
+    h = hashlib.sha256()
+    try:
+        for f in rec["sources"]:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    if h.hexdigest() != rec.get("sources_sha256") or rec.get("workload") != workload:
+        return None
+    return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+
+
 def cpu_oracle_rate(col, budget_s: float = 20.0):
     """The oracle as it stands, one host core: tuples/s over whole-column merges."""
     import oracle
@@ -300,7 +322,8 @@ def run_gpu(args):
     peak, peak_kind = measured_peaks()
     achieved = step2 / (reencode_ms / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "reencode_kernel<b>",
+                "frac": achieved / peak, "traffic": recorded_traffic("reencode_kernel", args.workload),
+                "kernel": "reencode_kernel<b>",
                 "algorithmic_bytes": step2, "peak_source": peak_kind,
                 "phase_ms_avg": {
                     "step1_kernel": (phase_ms[0] + phase_ms[1] + phase_ms[2]) / max(calls, 1),
