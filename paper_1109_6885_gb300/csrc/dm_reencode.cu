@@ -245,15 +245,20 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArg
         }
         uint32_t w[B];
         load_row<B>(stage + lane * B, w);
+        // unpacking consumes every word read from the stage, so after it (and
+        // the warp barrier) no lane has a read of the stage outstanding; the
+        // proxy fence then orders those reads before the bulk copy that
+        // refills the stage (generic-proxy reads, async-proxy write)
+        unpack32<B>(w, c);
         __syncwarp();
         if (lane == 0) {
+          fence_proxy_async_smem();
           uint64_t tn = t + (uint64_t)stages * nw;
           if (tn < full_tiles) {
             mbar_arrive_expect_tx(&bars[st], in_bytes);
             bulk_g2s(stage, a.main_words + tn * 32 * B, in_bytes, &bars[st]);
           }
         }
-        unpack32<B>(w, c);
         if (++st == stages) {
           st = 0;
           ph ^= 1u;

@@ -557,6 +557,22 @@ def test_tuning_changes_nothing(warps, stages, obufs):
     c.close()
 
 
+@pytest.mark.parametrize("flags", [0, "X_GLOBAL", "X_SMEM"])
+def test_merge_repeats_bulk_copy_ring(ctx, flags):
+    """A column whose re-encode once read a bulk-copy stage while the copy refilling it
+    landed (8M rows at 23 bits over 5.29M values, Zipf(0.8) codes, 80k delta rows): the
+    stage is refilled only after every lane's reads of it are done, so each repeat gives
+    the same bytes as the oracle."""
+    f = 0 if flags == 0 else getattr(dm, "DM_FLAG_" + flags)
+    spec = synth.ColumnSpec(n_main=8_000_000, m=5_293_474, w=8, n_delta=80_000, f_new=0.209218938724463,
+                            dist="zipf", zipf_s=0.8, seed=synth.column_seed(4, 41))
+    col = synth.make_column(spec)
+    assert col.main_bits == 23
+    ref = assert_parity(ctx, col, f)
+    for _ in range(3):
+        assert_parity(ctx, col, f, ref)
+
+
 @pytest.mark.parametrize("b_extra", [0, 1, 4])
 def test_reencode_directory_width_variants(ctx, b_extra):
     """Directory mode over codes stored wider than needed (covering and not)."""
