@@ -64,6 +64,7 @@ size_t carve_column(void* base, const dm_column_in* in, const dm_column_out* out
   void* xm = (out && out->x_main) ? nullptr : c.take(m * 4);
   void* xd = (out && out->x_delta) ? nullptr : c.take(d * 4);
   void* xdir = in->main_rows ? c.take((size_t)dm::reencode_dir_words() * 4) : nullptr;
+  void* cuts = c.take(((size_t)dm::merge_tiles(m + d, w) + 1) * 8);
   if (cs && base) {
     cs->zero = reinterpret_cast<uint32_t*>(zero);
     cs->zero_bytes = zero_bytes;
@@ -80,6 +81,7 @@ size_t carve_column(void* base, const dm_column_in* in, const dm_column_out* out
     a.final_slot = cs->slots;
     a.a = in->main_dict;
     a.m = m;
+    a.cuts = static_cast<uint64_t*>(cuts);
     cs->xm = (out && out->x_main) ? out->x_main : static_cast<uint32_t*>(xm);
     cs->xd = (out && out->x_delta) ? out->x_delta : static_cast<uint32_t*>(xd);
     a.xm = cs->xm;

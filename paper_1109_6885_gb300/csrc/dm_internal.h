@@ -40,6 +40,8 @@ struct Step1Args {
   uint32_t* d_bits;
   uint64_t* merge_lb;        // [merge_tiles] look-back words (zeroed)
   uint32_t merge_tiles;
+  uint64_t* cuts;            // optional [merge_tiles + 1]: U_M co-ranks of the tile boundaries,
+                             // computed up front when the merge takes several waves of tiles
   // directory of X_M for Step 2(b)
   uint32_t* xdir;
   uint32_t dir_shift;

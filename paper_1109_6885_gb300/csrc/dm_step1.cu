@@ -113,6 +113,7 @@ struct MergeSmem {
   uint64_t cut[2];
   uint64_t excl, lb_sum;
   uint32_t nearest;
+  uint32_t next_tile;
   K prevA, prevB;
 };
 
@@ -667,7 +668,7 @@ __device__ uint64_t corank_warp(const K* A, uint64_t m, const K* B, uint64_t d, 
 
 template <int W>
 __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename KeyOf<W>::T* B, const uint32_t* perm,
-                           bool bcoh, MergeSmem<W>& S) {
+                           bool bcoh, bool precut, MergeSmem<W>& S) {
   using K = typename KeyOf<W>::T;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const K* A = static_cast<const K*>(a.a);
@@ -677,7 +678,9 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   constexpr uint32_t E = T / S1_THREADS;     // U_M prefix entries per thread
   const uint64_t k0 = (uint64_t)tile * T;
   const uint64_t k1 = k0 + T < n ? k0 + T : n;
-  if (warp < 2) {
+  if (precut) {
+    if (tid < 2) S.cut[tid] = __ldcg(a.cuts + tile + tid);
+  } else if (warp < 2) {
     const uint64_t c = corank_warp(A, m, B, d, warp == 0 ? k0 : k1, bcoh);
     if (lane == 0) S.cut[warp] = c;
   }
@@ -717,6 +720,7 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   const K* sB = S.keys + na;
 
   // U_M must be strictly increasing
+#pragma unroll 4
   for (uint32_t x = tid; x < na; x += S1_THREADS) {
     if (i0 + x == 0) continue;
     const K prev = x > 0 ? sA[x - 1] : S.prevA;
@@ -852,6 +856,7 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   // threads, nearly consecutive codes); X_D is scattered through perm.
   const uint64_t excl = S.excl;
   K* unew = static_cast<K*>(a.unew);
+#pragma unroll 4
   for (uint32_t x = tid; x < na; x += S1_THREADS) {
     const uint64_t code = excl + x + S.ndx[S.cnt[x]];
     if (code < n) {
@@ -948,7 +953,31 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
     if (a.phases & (S1_MERGE | S1_DIR)) grid_barrier(a.barriers, nbar++, a.status);
   }
   if ((a.phases & S1_MERGE) && a.m + a.d > 0) {
-    for (uint32_t t = blockIdx.x; t < a.merge_tiles; t += gridDim.x) merge_tile<W>(a, t, ud, up, coherent, U.m);
+    // a merge of several waves of tiles finds every tile boundary first, one
+    // warp per boundary, so that each tile starts with its loads
+    const bool precut = a.cuts != nullptr && a.merge_tiles > gridDim.x;
+    if (precut) {
+      constexpr uint32_t T = MergeSmem<W>::T;
+      const uint64_t n = a.m + a.d;
+      const uint32_t lane = threadIdx.x & 31;
+      const uint32_t nwt = gridDim.x * S1_WARPS;
+      for (uint32_t b = blockIdx.x * S1_WARPS + (threadIdx.x >> 5); b <= a.merge_tiles; b += nwt) {
+        const uint64_t k = (uint64_t)b * T < n ? (uint64_t)b * T : n;
+        const uint64_t c = corank_warp(static_cast<const K*>(a.a), a.m, ud, a.d, k, coherent);
+        if (lane == 0) a.cuts[b] = c;
+      }
+      grid_barrier(a.barriers, nbar++, a.status);
+    }
+    // tiles are taken in index order from a counter, so that a tile's
+    // look-back only waits on tiles already being merged
+    uint32_t* next = a.barriers + S1_BARRIERS - 1;
+    for (;;) {
+      if (threadIdx.x == 0) U.m.next_tile = atomicAdd(next, 1u);
+      __syncthreads();
+      const uint32_t t = U.m.next_tile;
+      if (t >= a.merge_tiles) break;
+      merge_tile<W>(a, t, ud, up, coherent, precut, U.m);
+    }
   }
   if ((a.phases & S1_DIR) && a.dir_entries > 0) {
     grid_barrier(a.barriers, nbar++, a.status);
