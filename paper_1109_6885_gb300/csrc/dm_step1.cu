@@ -968,15 +968,16 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
       }
       grid_barrier(a.barriers, nbar++, a.status);
     }
-    // tiles are taken in index order from a counter, so that a tile's
-    // look-back only waits on tiles already being merged
+    // block b merges tile b; further tiles (a merge of several waves) are
+    // taken in index order from a counter, so that a tile's look-back only
+    // waits on tiles already being merged
     uint32_t* next = a.barriers + S1_BARRIERS - 1;
-    for (;;) {
-      if (threadIdx.x == 0) U.m.next_tile = atomicAdd(next, 1u);
-      __syncthreads();
-      const uint32_t t = U.m.next_tile;
-      if (t >= a.merge_tiles) break;
+    for (uint32_t t = blockIdx.x; t < a.merge_tiles;) {
       merge_tile<W>(a, t, ud, up, coherent, precut, U.m);
+      if (a.merge_tiles <= gridDim.x) break;
+      if (threadIdx.x == 0) U.m.next_tile = gridDim.x + atomicAdd(next, 1u);
+      __syncthreads();
+      t = U.m.next_tile;
     }
   }
   if ((a.phases & S1_DIR) && a.dir_entries > 0) {
