@@ -46,6 +46,7 @@ struct ColumnScratch {
   uint32_t* xm = nullptr;
   uint32_t* xd = nullptr;
   uint32_t* xdir = nullptr;   // directory of X_M for Step 2(b)
+  uint8_t* x8 = nullptr;      // its byte table
   void** slots = nullptr;
 };
 
@@ -64,12 +65,14 @@ size_t carve_column(void* base, const dm_column_in* in, const dm_column_out* out
   void* xm = (out && out->x_main) ? nullptr : c.take(m * 4);
   void* xd = (out && out->x_delta) ? nullptr : c.take(d * 4);
   void* xdir = in->main_rows ? c.take((size_t)dm::reencode_dir_words() * 4) : nullptr;
+  void* x8 = in->main_rows && dm::reencode_wants_x8(m) ? c.take(m) : nullptr;
   void* cuts = c.take(((size_t)dm::merge_tiles(m + d, w) + 1) * 8);
   if (cs && base) {
     cs->zero = reinterpret_cast<uint32_t*>(zero);
     cs->zero_bytes = zero_bytes;
     cs->slots = static_cast<void**>(slots);
     cs->xdir = static_cast<uint32_t*>(xdir);
+    cs->x8 = static_cast<uint8_t*>(x8);
     dm::Step1Args& a = cs->s1;
     dm::step1_layout(w, m + d, d, cs->zero, &a);
     a.in_keys = in->delta_dict;
@@ -149,6 +152,7 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
   ra.out_words = static_cast<uint32_t*>(out->new_packed);
   ra.status = ctx->status;
   ra.xdir = cs.xdir;
+  ra.x8 = cs.x8;
   ra.tune_warps = ctx->tuning.reencode_warps;
   ra.tune_stages = ctx->tuning.reencode_stages;
   ra.tune_obufs = ctx->tuning.reencode_obufs;
@@ -166,6 +170,7 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
     a.d_u = out->d_new_dict_len;
     a.d_bits = out->d_new_bits;
     a.xdir = cs.xdir;
+    a.x8 = plan.needs_directory ? cs.x8 : nullptr;
     a.dir_shift = plan.dir_shift;
     a.dir_entries = plan.dir_entries;
     a.status = ctx->status;
@@ -732,8 +737,13 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
   ra.max_bits = max_bits;
   ra.out_words = out_packed;
   ra.status = ctx->status;
-  // the X_M directory goes to the arena when it has room (else no directory)
-  ra.xdir = ctx->arena_bytes >= (size_t)dm::reencode_dir_words() * 4 ? static_cast<uint32_t*>(ctx->arena) : nullptr;
+  // the X_M directory goes to the arena when it has room (else no
+  // directory), its byte table after it when that fits too
+  const size_t dir_bytes = (size_t)dm::reencode_dir_words() * 4;
+  ra.xdir = ctx->arena_bytes >= dir_bytes ? static_cast<uint32_t*>(ctx->arena) : nullptr;
+  ra.x8 = ra.xdir && dm::reencode_wants_x8(m) && ctx->arena_bytes >= dir_bytes + m
+              ? static_cast<uint8_t*>(ctx->arena) + dir_bytes
+              : nullptr;
   ra.tune_warps = ctx->tuning.reencode_warps;
   ra.tune_stages = ctx->tuning.reencode_stages;
   ra.tune_obufs = ctx->tuning.reencode_obufs;

@@ -46,6 +46,7 @@ struct Step1Args {
   uint32_t* xdir;
   uint32_t dir_shift;
   uint32_t dir_entries;
+  uint8_t* x8;               // optional [m]: byte table for the directory's crowded buckets
   // control
   uint32_t phases;           // S1_SORT | S1_MERGE | S1_DIR
   uint32_t* barriers;        // [S1_BARRIERS] (zeroed)
@@ -88,12 +89,17 @@ struct ReencodeArgs {
   uint32_t* out_words;
   uint32_t* status;
   uint32_t* xdir;            // scratch for the X_M directory (reencode_dir_words() words) or NULL
+  uint8_t* x8;               // scratch for its byte table ([m]) or NULL
   uint32_t tune_warps;       // 0 = default; warps per block
   uint32_t tune_stages;      // 0 = default; input stages per warp
   uint32_t tune_obufs;       // 0 = default; output buffers per warp
 };
 
 uint32_t reencode_dir_words();
+// Most main codes a directory can cover (m above it: no directory, no byte table).
+uint64_t reencode_dir_max_codes();
+// Whether a column of m main codes gets the directory's byte table.
+bool reencode_wants_x8(uint64_t m);
 
 // Host-side launch plan of Step 2(b) (opaque storage).
 struct ReencodePlan {

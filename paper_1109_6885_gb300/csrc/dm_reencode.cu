@@ -40,6 +40,12 @@ namespace {
 constexpr uint32_t RE_STAGES_MAX = 4;
 constexpr uint32_t RE_TILE = 1024;          // codes per warp tile
 constexpr uint32_t RE_XSMEM_MAX = 16384;    // X_M entries staged in shared memory at most
+// Above this many main codes X_M (4 bytes a code) is unlikely to stay in L2
+// next to the streams, and the directory's crowded buckets read a byte table.
+constexpr uint64_t RE_X8_MIN_CODES = 8u << 20;
+// Input widths that can carry that many codes (the byte-table path is
+// compiled into their kernels only).
+constexpr bool RE_X8_B(int b) { return (1ull << b) > RE_X8_MIN_CODES; }
 
 template <int B>
 __device__ __forceinline__ void load_row(const uint32_t* row, uint32_t (&w)[B > 0 ? B : 1]) {
@@ -177,9 +183,11 @@ __host__ __device__ __forceinline__ uint32_t smem_bytes(const Layout& L, uint32_
 // The X_M directory (see dm_xdir.cuh) built by a kernel of its own when
 // Step 2(b) runs without the Step 1 kernel in front of it.
 __global__ void xdir_build_kernel(const uint32_t* __restrict__ xm, uint32_t m, uint32_t s, uint32_t R,
-                                  uint32_t* __restrict__ dir) {
-  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < R) dir[b] = xdir_entry<false>(xm, m, s, b);
+                                  uint32_t* __restrict__ dir, uint8_t* __restrict__ x8) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+  for (uint32_t b = t; b < R; b += nt) dir[b] = xdir_entry<false>(xm, m, s, b, x8 != nullptr);
+  if (x8)
+    for (uint32_t i = t; i < m; i += nt) x8[i] = xdir_x8<false>(xm, s, i);
 }
 
 template <int B>
@@ -207,6 +215,7 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArg
   constexpr uint32_t in_bytes = 128u * B;
   const uint32_t xmode = L.x_mode;
   const uint32_t dshift = L.dir_shift, dmask = (1u << L.dir_shift) - 1u;
+  const uint64_t stream_policy = policy_evict_first();   // the packed streams pass through once
 
   if (xmode != 0) {
     const uint32_t* src = xmode == 1 ? a.xm : a.xdir;
@@ -224,7 +233,7 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArg
         uint64_t t = gw + (uint64_t)s * nw;
         if (t < full_tiles) {
           mbar_arrive_expect_tx(&bars[s], in_bytes);
-          bulk_g2s(wbase + s * round4(L.in_words), a.main_words + t * 32 * B, in_bytes, &bars[s]);
+          bulk_g2s_hint(wbase + s * round4(L.in_words), a.main_words + t * 32 * B, in_bytes, &bars[s], stream_policy);
         }
       }
     }
@@ -256,7 +265,7 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArg
           uint64_t tn = t + (uint64_t)stages * nw;
           if (tn < full_tiles) {
             mbar_arrive_expect_tx(&bars[st], in_bytes);
-            bulk_g2s(stage, a.main_words + tn * 32 * B, in_bytes, &bars[st]);
+            bulk_g2s_hint(stage, a.main_words + tn * 32 * B, in_bytes, &bars[st], stream_policy);
           }
         }
         if (++st == stages) {
@@ -282,13 +291,23 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArg
           const uint32_t e = s_x[c[j] >> dshift];
           const uint32_t y = (c[j] & dmask) * (1u << 20) + e;   // multiply-add: FMA pipe
           x[j] = c[j] + (y & 0xFFFFFu) + __umulhi(y, 2u);        // y >> 31 on the FMA pipe
-          many |= ((e >> 20) == DIR_MANY_TOP ? 1u : 0u) << j;
+          many |= ((e >> 21) == DIR_SLOW ? 1u : 0u) << j;
         }
-        // codes in buckets with several steps read X_M itself
+        // codes in buckets with several steps read X_M, or the byte table
+        // where there is one (an X_M too large to stay in L2)
         if (__any_sync(0xFFFFFFFFu, many != 0)) {
+          if (!RE_X8_B(B) || a.x8 == nullptr) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if ((many >> j) & 1u) x[j] = __ldg(a.xm + c[j]);
+            for (int j = 0; j < 32; ++j)
+              if ((many >> j) & 1u) x[j] = __ldg(a.xm + c[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if ((many >> j) & 1u) {
+                const uint32_t e = s_x[c[j] >> dshift];
+                x[j] = (e >> 20) == DIR_MANY8_TOP ? c[j] + (e & 0xFFFFFu) + __ldg(a.x8 + c[j]) : __ldg(a.xm + c[j]);
+              }
+          }
         }
       } else if (xmode == 1) {
 #pragma unroll
@@ -402,7 +421,7 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArg
     const uint32_t tile_words = 32 * bo;
     if (w0 + tile_words <= out_total) {
       if (lane == 0 && bo > 0) {
-        bulk_s2g(a.out_words + w0, ob, tile_words * 4);
+        bulk_s2g_hint(a.out_words + w0, ob, tile_words * 4, stream_policy);
         bulk_commit();
       }
     } else {
@@ -457,6 +476,8 @@ Registry& registry() {
 }  // namespace
 
 uint32_t reencode_dir_words() { return RE_DIR_MAX; }
+uint64_t reencode_dir_max_codes() { return (uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX; }
+bool reencode_wants_x8(uint64_t m) { return m > RE_X8_MIN_CODES && m <= reencode_dir_max_codes(); }
 
 // Host-side launch plan of Step 2(b): lookup mode, block size, shared memory.
 struct ReencodePlanImpl {
@@ -541,7 +562,10 @@ cudaError_t launch_xdir(const ReencodePlan& plan, const ReencodeArgs& a, cudaStr
   ReencodePlanImpl P;
   memcpy(&P, plan.storage, sizeof(P));
   if (P.L.x_mode != 2) return cudaSuccess;
-  xdir_build_kernel<<<(P.L.x_entries + 255) / 256, 256, 0, s>>>(a.xm, a.m, P.L.dir_shift, P.L.x_entries, a.xdir);
+  const uint32_t work = a.x8 ? a.m : P.L.x_entries;
+  uint32_t blocks = (work + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  xdir_build_kernel<<<blocks, 256, 0, s>>>(a.xm, a.m, P.L.dir_shift, P.L.x_entries, a.xdir, a.x8);
   ++*launches;
   return cudaGetLastError();
 }

@@ -983,7 +983,10 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
   if ((a.phases & S1_DIR) && a.dir_entries > 0) {
     grid_barrier(a.barriers, nbar++, a.status);
     for (uint32_t b = blockIdx.x * S1_THREADS + threadIdx.x; b < a.dir_entries; b += gridDim.x * S1_THREADS)
-      a.xdir[b] = xdir_entry<true>(a.xm, (uint32_t)a.m, a.dir_shift, b);
+      a.xdir[b] = xdir_entry<true>(a.xm, (uint32_t)a.m, a.dir_shift, b, a.x8 != nullptr);
+    if (a.x8)
+      for (uint32_t i = blockIdx.x * S1_THREADS + threadIdx.x; i < a.m; i += gridDim.x * S1_THREADS)
+        a.x8[i] = xdir_x8<true>(a.xm, a.dir_shift, i);
   }
 }
 

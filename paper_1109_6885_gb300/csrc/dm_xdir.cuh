@@ -11,25 +11,33 @@
 // For a code i with offset lo = i mod 2^s in its bucket, entry + (lo << 20)
 // carries into bit 31 exactly when lo >= thr, so
 //   X_M[i] = i + (y & 0xFFFFF) + (y >> 31),  y = entry + (lo << 20).
-// A bucket without steps stores thr = 2047 (never reached); a bucket with
-// two or more steps, or whose base needs more than 20 bits, stores the
-// marker thr = 2046 and its codes read X_M itself.
+// A bucket without steps stores thr = 2047 (never reached).  A bucket with
+// two or more steps (up to 255) and a 20-bit base, when a byte table X8 of
+// c[i] - base exists, stores the marker thr = 2045 with its base, and its
+// codes read X8: X_M[i] = i + base + X8[i] (X8 is a quarter of X_M's size,
+// so it stays in L2 where X_M may not).  Other buckets store the marker
+// thr = 2046 and their codes read X_M itself.
 #pragma once
 
 #include <stdint.h>
 
 namespace dm {
 
-constexpr uint32_t DIR_NONE = 2047, DIR_MANY = 2046;
-constexpr uint32_t DIR_MANY_TOP = 2048 - DIR_MANY;   // top 12 bits of a marked entry
+constexpr uint32_t DIR_NONE = 2047, DIR_MANY = 2046, DIR_MANY8 = 2045;
+constexpr uint32_t DIR_MANY_TOP = 2048 - DIR_MANY;     // top 12 bits of an entry read through X_M
+constexpr uint32_t DIR_MANY8_TOP = 2048 - DIR_MANY8;   // top 12 bits of an entry read through X8
+// Both markers share entry >> 21 == 1 (no other entry has it: NONE has top
+// 1, a single step top 1025..2048).
+constexpr uint32_t DIR_SLOW = DIR_MANY_TOP >> 1;
+static_assert((DIR_MANY8_TOP >> 1) == DIR_SLOW && (2048 - DIR_NONE) >> 1 != DIR_SLOW, "markers");
 constexpr uint32_t RE_DIR_MAX = 16384;               // entries (64 KiB of shared memory)
 constexpr uint32_t RE_DIR_SHIFT_MAX = 10;
 
 // Entry of bucket b.  Coherent: X_M was written earlier in the same kernel,
 // so it is read through L2 (ld.global.cg), never from a stale L1 line.
 template <bool Coherent>
-__device__ __forceinline__ uint32_t xdir_entry(const uint32_t* __restrict__ xm, uint32_t m, uint32_t s,
-                                               uint32_t b) {
+__device__ __forceinline__ uint32_t xdir_entry(const uint32_t* __restrict__ xm, uint32_t m, uint32_t s, uint32_t b,
+                                               bool has_x8) {
   auto ld = [&](uint32_t i) { return Coherent ? __ldcg(xm + i) : __ldg(xm + i); };
   const uint32_t lo = b << s;
   const uint32_t hi = min(((b + 1) << s), m) - 1;
@@ -48,10 +56,20 @@ __device__ __forceinline__ uint32_t xdir_entry(const uint32_t* __restrict__ xm, 
     }
     thr = l - lo;
   } else {
-    thr = DIR_MANY;
+    thr = has_x8 && cnt <= 255 ? DIR_MANY8 : DIR_MANY;
   }
   if (base >= (1u << 20)) thr = DIR_MANY;
   return ((2048u - thr) << 20) | (thr == DIR_MANY ? 0u : base);
+}
+
+// X8[i] = c[i] - c[first code of i's bucket - 1] (mod 256); read only for
+// codes in buckets marked DIR_MANY8, where it is exact.
+template <bool Coherent>
+__device__ __forceinline__ uint8_t xdir_x8(const uint32_t* __restrict__ xm, uint32_t s, uint32_t i) {
+  auto ld = [&](uint32_t k) { return Coherent ? __ldcg(xm + k) : __ldg(xm + k); };
+  const uint32_t lo = (i >> s) << s;
+  const uint32_t base = lo == 0 ? 0u : ld(lo - 1) - (lo - 1);
+  return (uint8_t)((ld(i) - i) - base);
 }
 
 // Bucket shift and entry count of the directory for m main codes.
