@@ -573,6 +573,45 @@ def test_merge_repeats_bulk_copy_ring(ctx, flags):
         assert_parity(ctx, col, f, ref)
 
 
+def test_reencode_byte_table(ctx):
+    """Above 8M main codes the directory's crowded buckets read a byte table of c[i] - base:
+    12M codes with 60k new values (most buckets crowded), plus one insertion point with 300
+    new values (more than a byte holds: that bucket reads X_M)."""
+    import torch
+    rng = np.random.default_rng(8888)
+    m = 12_000_000
+    pts = np.concatenate([rng.integers(0, m + 1, 60_000), np.full(300, 5_000_001)])
+    pts.sort()
+    xm = (np.arange(m) + np.searchsorted(pts, np.arange(m), side="right")).astype(np.uint32)
+    u = m + pts.size
+    b, bo = synth.bits_for(m), synth.bits_for(u)
+    n_main, n_delta, d = 3_000_011, 1_000, 50
+    mc = rng.integers(0, m, n_main).astype(np.uint32)
+    mc[:5000] = rng.integers(4_999_900, 5_000_100, 5000)   # codes around the crowded point
+    dc = rng.integers(0, d, n_delta).astype(np.uint32)
+    xd = rng.integers(0, u, d).astype(np.uint32)
+    main = synth.pack(mc, b)
+    want = oracle.reencode(main, b, n_main, dc, xm, xd, bo)
+    out = torch.empty((dm.dm_packed_bytes(n_main + n_delta, bo) // 4,), dtype=torch.int32, device="cuda")
+    bits = torch.tensor([bo], dtype=torch.int32, device="cuda")
+    t = [dm.to_device(x) for x in (main, dc, xm, xd)]
+    for flags in (dm.DM_FLAG_X_SMEM, 0):
+        out.fill_(-1)
+        dm.dm_reencode(ctx, t[0], b, n_main, t[1], n_delta, t[2], m, t[3], d, bits, bo, out, None, flags)
+        torch.cuda.synchronize()
+        assert ctx.sync_status() == dm.DM_OK
+        assert np.array_equal(dm.to_host(out, np.uint32), want), flags
+
+
+def test_merge_column_byte_table(ctx):
+    """A whole merge whose X_M (9M values, 450k new) takes the byte table."""
+    spec = synth.ColumnSpec(n_main=10_000_000, m=9_000_000, w=8, n_delta=1_000_000, f_new=0.5,
+                            dist="zipf", zipf_s=0.8, seed=synth.column_seed(7, 1))
+    col = synth.make_column(spec)
+    ref = assert_parity(ctx, col)
+    assert ref.u - col.main_dict.shape[0] > 100_000
+
+
 @pytest.mark.parametrize("b_extra", [0, 1, 4])
 def test_reencode_directory_width_variants(ctx, b_extra):
     """Directory mode over codes stored wider than needed (covering and not)."""
