@@ -9,10 +9,9 @@ namespace dm {
 // ---------------------------------------------------------------- Step 1
 constexpr int RS_ITEMS = 4;       // keys per thread of a sort tile
 constexpr int RS_TILE = 256 * RS_ITEMS;   // keys per sort tile
-// Merged positions per merge tile: 4096 for 4- and 8-byte keys (a 100M-row
-// column's merge fits one wave of tiles), 2048 for 16-byte keys (shared
-// memory); MG_TILE_MIN bounds the tile count for any width.
-constexpr uint32_t mg_tile(uint32_t w) { return w == 16 ? 2048u : 4096u; }
+// Merged positions per merge tile (a 100M-row column's merge fits one wave
+// of tiles at two blocks per SM); MG_TILE_MIN bounds the tile count.
+constexpr uint32_t mg_tile(uint32_t) { return 4096u; }
 constexpr uint32_t MG_TILE_MIN = 2048;
 constexpr uint32_t S1_SORT = 1, S1_MERGE = 2, S1_DIR = 4;   // phases
 constexpr uint32_t S1_BARRIERS = 32;                        // barrier counters per launch

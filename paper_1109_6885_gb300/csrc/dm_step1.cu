@@ -105,9 +105,10 @@ struct MergeSmem {
   using K = typename KeyOf<W>::T;
   static constexpr uint32_t T = mg_tile(W);
   K keys[T];                       // U_M segment then U_D segment
-  uint32_t perm[T];                // insertion codes of the U_D segment
+  // [0, na): per U_M entry, the U_D entries placed right before it, then
+  // their prefix; [na, na + nb): the U_D segment's insertion codes
+  alignas(16) uint32_t ap[T];
   uint32_t rank[T];                // per U_D entry: U_M entries of the tile at or below it
-  alignas(16) uint32_t cnt[T];     // per U_M entry: U_D entries placed right before it, then the prefix
   uint32_t ndx[T + 1];             // per U_D entry: non-duplicate U_D entries before it (and the total)
   uint32_t wsum[S1_WARPS];
   uint64_t cut[2];
@@ -130,17 +131,31 @@ struct BucketSmem {
 };
 constexpr uint32_t BK_SUB_MAX = 32;   // largest sub-bucket one thread sorts by insertion
 
+// The sort plan (first slot of every digit) lives in front of the sort and
+// bucket phases' memory; the merge phase, which no longer needs it, reuses
+// the whole union.
+template <int W>
+struct SortPhase {
+  uint32_t plan[W * 256];
+  SortSmem<W> s;
+};
+template <int W>
+struct BucketPhase {
+  uint32_t plan[W * 256];
+  BucketSmem<W> b;
+};
+
 template <int W>
 union Step1Smem {
-  SortSmem<W> s;
+  SortPhase<W> sp;
+  BucketPhase<W> bp;
   MergeSmem<W> m;
-  BucketSmem<W> b;
   uint32_t hist[W * 256];
 };
 
 template <int W>
 constexpr size_t step1_smem_bytes() {
-  return (sizeof(Step1Smem<W>) + 15) / 16 * 16 + (size_t)W * 256 * 4 + 64;
+  return (sizeof(Step1Smem<W>) + 15) / 16 * 16 + 64;
 }
 
 // ---------------------------------------------------------------- Step 1(a)
@@ -688,31 +703,36 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   const uint64_t i0 = S.cut[0], i1 = S.cut[1];
   const uint64_t j0 = k0 - i0, j1 = k1 - i1;
   const uint32_t na = (uint32_t)(i1 - i0), nb = (uint32_t)(j1 - j0), nt = na + nb;
-  // one batch of loads (all in flight before the first store): both
-  // segments, their perm entries, and the keys just before the tile (merge
-  // predecessor and sortedness check)
+  // the segments, their perm entries, and the keys just before the tile
+  // (merge predecessor and sortedness check), in batches whose loads are
+  // all in flight before the first store (two batches for 16-byte keys,
+  // for registers)
+  if (tid == 0 && i0 > 0) S.prevA = load_key(A + i0 - 1);
+  if (tid == 32 && j0 > 0) S.prevB = ld_key(B + j0 - 1, bcoh);
   {
     constexpr uint32_t R = T / S1_THREADS;
-    K kr[R];
-    uint32_t pr[R];
+    constexpr uint32_t RB = W == 16 ? R / 2 : R;   // loads per batch
 #pragma unroll
-    for (uint32_t r = 0; r < R; ++r) {
-      const uint32_t x = tid + r * S1_THREADS;
-      if (x < na) {
-        kr[r] = load_key(A + i0 + x);
-      } else if (x < nt) {
-        kr[r] = ld_key(B + j0 + (x - na), bcoh);
-        pr[r] = bcoh ? __ldcg(perm + j0 + (x - na)) : __ldg(perm + j0 + (x - na));
+    for (uint32_t r0 = 0; r0 < R; r0 += RB) {
+      K kr[RB];
+      uint32_t pr[RB];
+#pragma unroll
+      for (uint32_t r = 0; r < RB; ++r) {
+        const uint32_t x = tid + (r0 + r) * S1_THREADS;
+        if (x < na) {
+          kr[r] = load_key(A + i0 + x);
+        } else if (x < nt) {
+          kr[r] = ld_key(B + j0 + (x - na), bcoh);
+          pr[r] = bcoh ? __ldcg(perm + j0 + (x - na)) : __ldg(perm + j0 + (x - na));
+        }
       }
-    }
-    if (tid == 0 && i0 > 0) S.prevA = load_key(A + i0 - 1);
-    if (tid == 32 && j0 > 0) S.prevB = ld_key(B + j0 - 1, bcoh);
 #pragma unroll
-    for (uint32_t r = 0; r < R; ++r) {
-      const uint32_t x = tid + r * S1_THREADS;
-      if (x < nt) S.keys[x] = kr[r];
-      if (x >= na && x < nt) S.perm[x - na] = pr[r];
-      S.cnt[x] = 0;
+      for (uint32_t r = 0; r < RB; ++r) {
+        const uint32_t x = tid + (r0 + r) * S1_THREADS;
+        if (x < nt) S.keys[x] = kr[r];
+        if (x < na) S.ap[x] = 0;
+        else if (x < nt) S.ap[x] = pr[r];
+      }
     }
   }
   __syncthreads();
@@ -742,7 +762,7 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
         r = (p <= na && key_le(v, x)) ? p : r;
       }
       S.rank[j] = r;
-      if (r < na) atomicAdd(&S.cnt[r], 1u);
+      if (r < na) atomicAdd(&S.ap[r], 1u);
     }
   }
   __syncthreads();
@@ -767,16 +787,18 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
     return has_prev && key_eq(sB[j], pk) ? 0u : 1u;
   };
   // U_D entries placed before this thread's U_M entries [Et, Et + E)
+  // (entries at or past na hold insertion codes: they count as zero)
   uint32_t cinc[E];
   {
     uint32_t run = 0;
 #pragma unroll
     for (uint32_t v = 0; v < E / 4; ++v) {
-      const uint4 c = reinterpret_cast<const uint4*>(S.cnt)[(E / 4) * tid + v];
-      cinc[4 * v] = run += c.x;
-      cinc[4 * v + 1] = run += c.y;
-      cinc[4 * v + 2] = run += c.z;
-      cinc[4 * v + 3] = run += c.w;
+      const uint32_t i = E * tid + 4 * v;
+      const uint4 c = reinterpret_cast<const uint4*>(S.ap)[(E / 4) * tid + v];
+      cinc[4 * v] = run += i < na ? c.x : 0u;
+      cinc[4 * v + 1] = run += i + 1 < na ? c.y : 0u;
+      cinc[4 * v + 2] = run += i + 2 < na ? c.z : 0u;
+      cinc[4 * v + 3] = run += i + 3 < na ? c.w : 0u;
     }
   }
   // the U_M prefix and the first round of U_D non-duplicates in one block
@@ -786,9 +808,17 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   {
     const uint32_t cx = pex & 0xFFFFu;
 #pragma unroll
-    for (uint32_t v = 0; v < E / 4; ++v)
-      reinterpret_cast<uint4*>(S.cnt)[(E / 4) * tid + v] =
-          make_uint4(cx + cinc[4 * v], cx + cinc[4 * v + 1], cx + cinc[4 * v + 2], cx + cinc[4 * v + 3]);
+    for (uint32_t v = 0; v < E / 4; ++v) {
+      const uint32_t i = E * tid + 4 * v;
+      if (i + 3 < na) {
+        reinterpret_cast<uint4*>(S.ap)[(E / 4) * tid + v] =
+            make_uint4(cx + cinc[4 * v], cx + cinc[4 * v + 1], cx + cinc[4 * v + 2], cx + cinc[4 * v + 3]);
+      } else {
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q)
+          if (i + q < na) S.ap[i + q] = cx + cinc[4 * v + q];
+      }
+    }
   }
   if (tid < nb) S.ndx[tid] = pex >> 16;
   uint32_t ndB = total >> 16;
@@ -858,7 +888,7 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   K* unew = static_cast<K*>(a.unew);
 #pragma unroll 4
   for (uint32_t x = tid; x < na; x += S1_THREADS) {
-    const uint64_t code = excl + x + S.ndx[S.cnt[x]];
+    const uint64_t code = excl + x + S.ndx[S.ap[x]];
     if (code < n) {
       unew[code] = sA[x];
       a.xm[i0 + x] = (uint32_t)code;
@@ -875,7 +905,7 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
       continue;
     }
     if (nondup) unew[code] = sB[j];
-    const uint32_t pj = S.perm[j];
+    const uint32_t pj = S.ap[na + j];
     if (pj < d) a.xd[pj] = (uint32_t)code;
     else flag_status(a.status, ST_CODE);
   }
@@ -893,8 +923,8 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
   using K = typename KeyOf<W>::T;
   extern __shared__ __align__(16) unsigned char dsmem[];
   Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
-  uint32_t* s_plan = reinterpret_cast<uint32_t*>(dsmem + (sizeof(Step1Smem<W>) + 15) / 16 * 16);
-  uint32_t* s_wsum = s_plan + W * 256;
+  uint32_t* s_plan = U.sp.plan;   // the same words as U.bp.plan
+  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(Step1Smem<W>) + 15) / 16 * 16);
 
   uint32_t nbar = 0;
   const K* ud = static_cast<const K*>(a.b);
@@ -905,7 +935,7 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
     uint32_t* v0 = a.vals[0];
     if (a.d <= BK_SINGLE) {
       // a delta dictionary this small is sorted by one block
-      if (blockIdx.x == 0) bucket_sort<W>(static_cast<const K*>(a.in_keys), nullptr, 0, (uint32_t)a.d, false, k0, v0, U.b);
+      if (blockIdx.x == 0) bucket_sort<W>(static_cast<const K*>(a.in_keys), nullptr, 0, (uint32_t)a.d, false, k0, v0, U.bp.b);
       ud = k0;
       up = v0;
     } else {
@@ -917,7 +947,7 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
         // one stable pass on the top varying digit, then each of its 256
         // buckets sorted in shared memory in place
         const int top = 31 - __clz(run);
-        for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) msd_tile<W>(a, top, t, s_plan, U.s);
+        for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) msd_tile<W>(a, top, t, s_plan, U.sp.s);
         grid_barrier(a.barriers, nbar++, a.status);
         // the next byte below the top one that varies splits each bucket once more
         const uint32_t lower = run & ((1u << top) - 1u);
@@ -926,8 +956,8 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
           const uint32_t off = s_plan[top * 256 + b];
           const uint32_t n = (b < 255 ? s_plan[top * 256 + b + 1] : (uint32_t)a.d) - off;
           if (n <= 1) continue;
-          if (sub >= 0) bucket_sort_sub<W>(k0, v0, off, n, true, k0, v0, sub, U.b);
-          else bucket_sort<W>(k0, v0, off, n, true, k0, v0, U.b);
+          if (sub >= 0) bucket_sort_sub<W>(k0, v0, off, n, true, k0, v0, sub, U.bp.b);
+          else bucket_sort<W>(k0, v0, off, n, true, k0, v0, U.bp.b);
         }
         ud = k0;
         up = v0;
@@ -935,7 +965,7 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
         int e = 0;
         for (int p = 0; p < W; ++p) {
           if (!((run >> p) & 1u)) continue;
-          for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) pass_tile<W>(a, p, t, e, s_plan, U.s);
+          for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) pass_tile<W>(a, p, t, e, s_plan, U.sp.s);
           grid_barrier(a.barriers, nbar++, a.status);
           ++e;
         }
