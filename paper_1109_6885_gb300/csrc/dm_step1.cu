@@ -11,13 +11,16 @@
 // slot of every digit, bytes whose digit is not constant).  When every
 // bucket of the most significant varying byte holds at most 2048 keys, one
 // partition pass scatters the keys into those buckets (atomic cursors) and
-// each bucket is merge-sorted in shared memory by (key, insertion code);
+// each block sorts a bucket in shared memory by (key, insertion code):
+// a count/scatter on the next varying byte into 256 sub-buckets, each
+// finished by one thread's insertion sort, or a block merge sort when a
+// sub-bucket holds more than 32 keys;
 // otherwise stable LSD passes run, each ranking 1024-key tiles with a warp
 // multisplit and a decoupled look-back over earlier tiles.
 //
 // Step 1(b).  The paper cuts both dictionaries at N_T-quantiles and fixes
 // the output offsets with a counter array and a prefix sum (Section 6.2.1).
-// Here tile t owns merged positions [2048t, 2048t + 2048): a merge-path
+// Here tile t owns merged positions [4096t, 4096t + 4096): a merge-path
 // (co-rank) search cuts U_M and U_D (ties: the main value first).  Inside
 // the tile, each U_D entry is ranked against the U_M segment by binary
 // search; a U_D entry is a duplicate when it equals the key before it in
