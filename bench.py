@@ -83,6 +83,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="table workloads: run on the library defaults instead of tuned launch choices")
+    p.add_argument("--tune-cache", default=None,
+                   help="table workloads: load tuned choices from this JSON file first, save them after")
     return p.parse_args()
 
 
@@ -511,6 +515,26 @@ def run_table(args):
         rate = shard.aggregate_rate(tuples * args.steps, total / 1e3, "cuda")
         return 1e3 * shard.max_over_ranks(total / 1e3, "cuda"), per, rate
 
+    # autotuning: the batched form on library defaults first, then every
+    # column class tuned (outside the timed regions), then both forms on the
+    # tuned choices
+    tune = None
+    if not args.no_autotune:
+        t_default, _, _ = timed(0)
+        cache = ctx.tune_cache
+        if args.tune_cache and os.path.exists(args.tune_cache):
+            cache.load(args.tune_cache)
+        n0 = len(cache)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dm.dm_merge_table(ctx, cins, couts, stream, dm.DM_FLAG_AUTOTUNE)
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t0
+        if args.tune_cache:
+            cache.save(args.tune_cache)
+        classes = {dm.dm_tune_key_of(ci).as_tuple() for ci in cins}
+        tune = {"classes": len(classes), "tuned_now": len(cache) - n0, "tuning_s": tune_s,
+                "defaults_ms_per_step": t_default / args.steps}
     launches0 = ctx.launches
     sampler = ClockSampler(local, not args.no_clocks)
     sampler.wait_ready()
@@ -518,6 +542,8 @@ def run_table(args):
     clocks = sampler.stop()
     launches = (ctx.launches - launches0) // (args.steps + max(args.warmup, 3))
     t_serial, per_s, rate_s = timed(dm.DM_FLAG_SERIAL)
+    if tune is not None:
+        tune["speedup_vs_defaults"] = tune["defaults_ms_per_step"] / (t_batched / args.steps)
     step2 = 0
     for c, r in zip(cols, res):
         u, b = r.u_bits()
@@ -533,6 +559,7 @@ def run_table(args):
             "vs_baseline": None, "dtype": "mixed u32/u64/u128", "data": "synthetic",
             "config": {"workload": args.workload, **TABLES[args.workload],
                        "form": "one CUDA-graph launch per table (4 branches)",
+                       "launch_choices": "autotuned per column class" if tune else "library defaults",
                        "parallelism": f"the table's {len(specs)} columns shared over {world} GPU(s), longest first",
                        "l2": "inputs larger than L2"},
             "latency_ms": {"p50": pct(per_b, 0.5), "p99": pct(per_b, 0.99)},
@@ -544,6 +571,8 @@ def run_table(args):
             "table_hbm_gbs_effective": step2 / (t_batched / args.steps / 1e3) / 1e9, "hbm_peak_gbs": peak,
             "gpu_launches": launches, "clocks": clocks,
         }
+        if tune is not None:
+            line["autotune"] = tune
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

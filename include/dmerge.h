@@ -70,7 +70,8 @@ typedef enum {
   DM_ECODE = 4,      /* a main code >= |U_M| or a delta code >= |D_dict| */
   DM_ECUDA = 5,      /* a CUDA runtime call failed */
   DM_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
-  DM_EBUSY = 7       /* the request cannot be admitted now */
+  DM_EBUSY = 7,      /* the request cannot be admitted now */
+  DM_ENOENT = 8      /* no such entry (tune cache lookup, missing file) */
 } dm_status;
 
 /* flags for dm_merge_column / dm_merge_table */
@@ -79,8 +80,13 @@ typedef enum {
 #define DM_FLAG_X_GLOBAL 0x4u          /* never stage X_M in shared memory */
 #define DM_FLAG_TIMING 0x8u            /* record per-step CUDA events (dm_last_timing) */
 #define DM_FLAG_SERIAL 0x10u           /* dm_merge_table: one column after another, plain launches */
+#define DM_FLAG_AUTOTUNE 0x20u         /* dm_merge_column / dm_merge_table: first tune every column
+                                          class missing from the tune cache (dm_autotune_column;
+                                          blocks the host while it runs) */
 
 typedef struct dm_ctx dm_ctx;
+/* Launch choices per column class (see "autotuning" below). */
+typedef struct dm_tune_cache dm_tune_cache;
 
 /* Create a context on `device` with a scratch arena of arena_bytes (may be
  * 0; grow it later with dm_reserve).  Synchronous. */
@@ -257,6 +263,11 @@ typedef struct {
 } dm_server_stats;
 
 dm_status dm_server_create(dm_server** server, int device, const dm_server_config* cfg);
+/* The tune cache every slot of the server looks its choices up in (owned
+ * by the server): load a saved cache into it before submitting, since
+ * tuning inside a slot (DM_FLAG_AUTOTUNE in cfg.flags) times merges while
+ * other slots run. */
+dm_tune_cache* dm_server_tune_cache(dm_server* server);
 /* Stops the scheduler thread (pending requests are dropped) and frees the pool. */
 void dm_server_destroy(dm_server* server);
 /* Register table `table_id`: ncols columns (device pointers, caller-owned,
@@ -315,6 +326,100 @@ typedef struct {
 
 dm_status dm_set_tuning(dm_ctx* ctx, const dm_tuning* tuning);
 dm_status dm_get_tuning(const dm_ctx* ctx, dm_tuning* tuning);
+
+/* ---- autotuning ----
+ *
+ * The paper's table merge treats every column as an independent task
+ * (Section 6.2.1, scheme (i)); which launch shape runs a column fastest
+ * depends on the column's widths and sizes, not on the method.  The
+ * autotuner times whole-column merges under candidate launch choices and
+ * keeps the fastest per column class in a tune cache; later merges of a
+ * class look its choice up.  Every choice gives byte-identical results.
+ *
+ * Precedence: non-zero dm_tuning fields and the DM_FLAG_X_SMEM /
+ * DM_FLAG_X_GLOBAL flags override the cache's choice; a cache field of 0
+ * means the library default. */
+
+
+/* Class of a column: its widths and the bit lengths (floor(log2 v) + 1, 0
+ * for v = 0) of its sizes. */
+typedef struct {
+  uint32_t value_bytes;        /* w */
+  uint32_t main_bits;          /* E_C */
+  uint32_t max_bits;           /* dm_max_bits: bound of E'_C */
+  uint32_t log2_m;             /* bit length of |U_M| */
+  uint32_t log2_d;             /* bit length of |D_dict| */
+  uint32_t log2_main_rows;     /* bit length of N_M */
+  uint32_t log2_delta_rows;    /* bit length of N_D */
+  uint32_t reserved;
+} dm_tune_key;
+
+#define DM_STAGE_AUTO 0u     /* X_M lookup: library rule (shared memory from 2^20 main rows) */
+#define DM_STAGE_SMEM 1u     /* X_M in shared memory (table or directory of its steps) when it fits */
+#define DM_STAGE_GLOBAL 2u   /* X_M gathered through L1/L2 */
+#define DM_X8_AUTO 0u        /* byte table for crowded directory buckets above 2^23 main codes */
+#define DM_X8_OFF 1u         /* no byte table: crowded buckets read X_M */
+
+/* Launch choices for one column class (0 = library default). */
+typedef struct {
+  uint32_t reencode_warps;     /* Step 2(b): warps per block (1..16) */
+  uint32_t reencode_stages;    /* Step 2(b): input bulk-copy stages per warp (2..4) */
+  uint32_t reencode_obufs;     /* Step 2(b): output staging buffers per warp (1..2) */
+  uint32_t x_staging;          /* DM_STAGE_* */
+  uint32_t x8;                 /* DM_X8_* */
+  uint32_t step1_blocks;       /* Step 1 grid: at most this many blocks (0: all that fit) */
+  uint32_t reserved[2];
+} dm_tune_choice;
+
+/* What dm_autotune_column measured. */
+typedef struct {
+  dm_tune_key key;             /* the class tuned */
+  dm_tune_choice best;         /* stored in the cache */
+  float best_ms;               /* median whole-merge milliseconds of `best` */
+  float default_ms;            /* the same for the library defaults */
+  uint32_t candidates;         /* choices timed */
+  uint32_t reps;               /* timed merges per choice */
+} dm_tune_report;
+
+/* The class of a column (host only; no device needed). */
+dm_status dm_tune_key_of(const dm_column_in* in, dm_tune_key* key);
+
+/* A tune cache is host memory only and thread-safe; contexts may share one.
+ * Every context starts with a cache of its own. */
+dm_status dm_tune_cache_create(dm_tune_cache** cache);
+void dm_tune_cache_destroy(dm_tune_cache* cache);
+/* Insert or replace the choice of a class (DM_EINVAL: a field out of range). */
+dm_status dm_tune_cache_put(dm_tune_cache* cache, const dm_tune_key* key, const dm_tune_choice* choice);
+/* The choice of a class, or DM_ENOENT. */
+dm_status dm_tune_cache_get(const dm_tune_cache* cache, const dm_tune_key* key, dm_tune_choice* choice);
+uint64_t dm_tune_cache_size(const dm_tune_cache* cache);
+/* Changes with every put, clear and load. */
+uint64_t dm_tune_cache_generation(const dm_tune_cache* cache);
+dm_status dm_tune_cache_clear(dm_tune_cache* cache);
+/* Write every entry to `path` as JSON; read such a file and merge its
+ * entries in (file entries replace equal keys).  A malformed file returns
+ * DM_EINVAL and changes nothing; a missing one DM_ENOENT. */
+dm_status dm_tune_cache_save(const dm_tune_cache* cache, const char* path);
+dm_status dm_tune_cache_load(dm_tune_cache* cache, const char* path);
+
+/* Use `cache` (not owned; it must outlive its use) for this context's
+ * lookups and tuning; NULL returns to the context's own cache. */
+dm_status dm_set_tune_cache(dm_ctx* ctx, dm_tune_cache* cache);
+dm_tune_cache* dm_get_tune_cache(dm_ctx* ctx);
+
+/* Every candidate choice the autotuner considers for `in` on this context's
+ * device: writes up to `cap` of them to `out` and returns how many exist. */
+uint32_t dm_tune_candidates(const dm_ctx* ctx, const dm_column_in* in, dm_tune_choice* out, uint32_t cap);
+
+/* Merge the column (as dm_merge_column) under candidate choices, timing
+ * `reps` merges of each (0: 5) with CUDA events on `stream`, and store the
+ * fastest in the context's tune cache.  The search takes the X_M staging
+ * and byte-table choices first, then the Step 2(b) launch shape, then the
+ * Step 1 grid, each time keeping the fastest so far.  On return `out` holds
+ * the merge result.  Synchronous (blocks the host); not inside a stream
+ * capture. */
+dm_status dm_autotune_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* stream,
+                             uint32_t flags, uint32_t reps, dm_tune_report* report);
 
 /* Kernels this context has launched so far. */
 uint64_t dm_launch_count(const dm_ctx* ctx);

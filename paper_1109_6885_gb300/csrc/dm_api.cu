@@ -121,6 +121,92 @@ dm_status check_column(const dm_column_in* in, const dm_column_out* out, bool de
 
 dm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DM_OK : DM_ECUDA; }
 
+// Launch choices in effect for one column.  A forced choice (the
+// autotuner's candidates) is taken as it is; otherwise non-zero dm_tuning
+// fields and the X_M staging flags come first, then the tune cache's entry
+// for the column's class, then the library defaults (zeros).
+struct Resolved {
+  uint32_t warps, stages, obufs;
+  uint32_t flags;          // the call's flags with the staging choice applied
+  uint32_t step1_blocks;   // 0: every block that fits
+  bool x8;
+};
+
+Resolved resolve(const dm_ctx* ctx, const dm_column_in* in, uint32_t flags, const dm_tune_choice* force) {
+  dm_tune_choice c{};
+  flags &= ~DM_FLAG_AUTOTUNE;
+  if (force) {
+    c = *force;
+    flags &= ~(DM_FLAG_X_SMEM | DM_FLAG_X_GLOBAL);
+  } else if (ctx->tune_cache->size.load(std::memory_order_relaxed)) {
+    const dm_tune_key k = dm::tune_key_of(*in);
+    if (dm_tune_cache_get(ctx->tune_cache, &k, &c) != DM_OK) c = dm_tune_choice{};
+  }
+  Resolved r;
+  const bool expl = force == nullptr;
+  r.warps = expl && ctx->tuning.reencode_warps ? ctx->tuning.reencode_warps : c.reencode_warps;
+  r.stages = expl && ctx->tuning.reencode_stages ? ctx->tuning.reencode_stages : c.reencode_stages;
+  r.obufs = expl && ctx->tuning.reencode_obufs ? ctx->tuning.reencode_obufs : c.reencode_obufs;
+  r.flags = flags;
+  if (!(flags & (DM_FLAG_X_SMEM | DM_FLAG_X_GLOBAL))) {
+    if (c.x_staging == DM_STAGE_SMEM) r.flags |= DM_FLAG_X_SMEM;
+    else if (c.x_staging == DM_STAGE_GLOBAL) r.flags |= DM_FLAG_X_GLOBAL;
+  }
+  r.step1_blocks = c.step1_blocks;
+  r.x8 = c.x8 != DM_X8_OFF;
+  return r;
+}
+
+// A column with rows whose class the context's tune cache lacks.
+bool needs_tuning(const dm_ctx* ctx, const dm_column_in* in) {
+  if (in->main_rows + in->delta_rows == 0) return false;
+  const dm_tune_key k = dm::tune_key_of(*in);
+  dm_tune_choice c;
+  return dm_tune_cache_get(ctx->tune_cache, &k, &c) == DM_ENOENT;
+}
+
+// The autotuner's candidate choices for a column: X_M staging (shared
+// memory or an L1/L2 gather, and the byte table where one is built) x
+// Step 2(b) launch shape (warps, input stages, output buffers; the first is
+// the default) x Step 1 grid (all blocks that fit, one per SM, a quarter).
+std::vector<dm_tune_choice> tune_candidates(const dm_ctx* ctx, const dm_column_in* in) {
+  static const uint32_t kShapes[][3] = {{0, 0, 0}, {16, 3, 1}, {16, 2, 2}, {8, 2, 1},
+                                        {8, 3, 1}, {4, 2, 1}, {4, 4, 2}};
+  std::vector<uint32_t> stagings = {DM_STAGE_AUTO};
+  if (in->main_rows) stagings = {DM_STAGE_SMEM, DM_STAGE_GLOBAL};
+  std::vector<uint32_t> x8s = {DM_X8_AUTO};
+  if (in->main_rows && dm::reencode_wants_x8(in->main_dict_len)) x8s.push_back(DM_X8_OFF);
+  const uint32_t grids[] = {0, ctx->sm_count, std::max<uint32_t>(1, ctx->sm_count / 4)};
+  std::vector<dm_tune_choice> v;
+  for (uint32_t st : stagings)
+    for (uint32_t x8 : x8s)
+      for (const auto& sh : kShapes)
+        for (uint32_t g : grids) {
+          dm_tune_choice c{};
+          c.x_staging = st;
+          c.x8 = x8;
+          c.reencode_warps = sh[0];
+          c.reencode_stages = sh[1];
+          c.reencode_obufs = sh[2];
+          c.step1_blocks = g;
+          v.push_back(c);
+        }
+  return v;
+}
+
+// Step 2(b) arguments that only the launch plan reads (sizes, tuning).
+dm::ReencodeArgs plan_args(const dm_column_in* in, const Resolved& r) {
+  dm::ReencodeArgs ra{};
+  ra.n_main = in->main_rows;
+  ra.n_delta = in->delta_rows;
+  ra.m = (uint32_t)std::min<uint64_t>(in->main_dict_len, 0xFFFFFFFFu);
+  ra.max_bits = bits_for(in->main_dict_len + in->delta_dict_len);
+  ra.tune_warps = r.warps;
+  ra.tune_stages = r.stages;
+  ra.tune_obufs = r.obufs;
+  return ra;
+}
+
 // Steps 1(a)..2(b) of one column whose scratch is laid out at `base`.
 // ev: five events recorded before Step 1, after the sort, after the merge
 // and the X_M directory (one kernel: both at its end), before the Step 2(b)
@@ -128,37 +214,33 @@ dm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? DM_OK : DM_ECUD
 dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* base,
                      cudaStream_t s, uint32_t flags, cudaEvent_t* ev, const dm::ReencodePlan* pre_plan = nullptr,
                      uint32_t grid_cap = 0, dm::ReencodePlan* plan_out = nullptr,
-                     dm::ReencodeArgs* args_out = nullptr) {
+                     dm::ReencodeArgs* args_out = nullptr, const dm_tune_choice* force = nullptr) {
   const bool timing = ev != nullptr;
   ColumnScratch cs;
   carve_column(base, in, out, &cs);
   const uint32_t w = in->value_bytes;
   const uint64_t m = in->main_dict_len, d = in->delta_dict_len;
   const uint64_t n_out = in->main_rows + in->delta_rows;
+  const Resolved rs = resolve(ctx, in, flags, force);
 
   // Step 2(b) launch plan first: it says whether Step 1 builds a directory
-  dm::ReencodeArgs ra{};
+  dm::ReencodeArgs ra = plan_args(in, rs);
   ra.main_words = static_cast<const uint32_t*>(in->main_packed);
   ra.main_words_n = dm_packed_bytes(in->main_rows, in->main_bits) / 4;
-  ra.n_main = in->main_rows;
   ra.dcodes = in->delta_codes;
-  ra.n_delta = in->delta_rows;
   ra.xm = cs.xm;
-  ra.m = (uint32_t)std::min<uint64_t>(m, 0xFFFFFFFFu);
   ra.xd = cs.xd;
   ra.d = (uint32_t)d;
   ra.d_bits = out->d_new_bits;
-  ra.max_bits = bits_for(m + d);
   ra.out_words = static_cast<uint32_t*>(out->new_packed);
   ra.status = ctx->status;
   ra.xdir = cs.xdir;
-  ra.x8 = cs.x8;
-  ra.tune_warps = ctx->tuning.reencode_warps;
-  ra.tune_stages = ctx->tuning.reencode_stages;
-  ra.tune_obufs = ctx->tuning.reencode_obufs;
+  ra.x8 = rs.x8 ? cs.x8 : nullptr;
   dm::ReencodePlan plan{};
   if (pre_plan) plan = *pre_plan;
-  else if (n_out && dm::plan_reencode(in->main_bits, ra, ctx->sm_count, flags, &plan) != cudaSuccess) return DM_ECUDA;
+  else if (n_out && dm::plan_reencode(in->main_bits, ra, ctx->sm_count, rs.flags, &plan) != cudaSuccess)
+    return DM_ECUDA;
+  if (rs.step1_blocks && (!grid_cap || rs.step1_blocks < grid_cap)) grid_cap = rs.step1_blocks;
 
   cudaError_t e = cudaMemsetAsync(cs.zero, 0, cs.zero_bytes, s);
   if (e != cudaSuccess) return DM_ECUDA;
@@ -170,7 +252,7 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
     a.d_u = out->d_new_dict_len;
     a.d_bits = out->d_new_bits;
     a.xdir = cs.xdir;
-    a.x8 = plan.needs_directory ? cs.x8 : nullptr;
+    a.x8 = plan.needs_directory ? ra.x8 : nullptr;
     a.dir_shift = plan.dir_shift;
     a.dir_entries = plan.dir_entries;
     a.status = ctx->status;
@@ -224,6 +306,7 @@ const char* dm_status_str(dm_status s) {
     case DM_ECUDA: return "DM_ECUDA";
     case DM_ETIMEOUT: return "DM_ETIMEOUT";
     case DM_EBUSY: return "DM_EBUSY";
+    case DM_ENOENT: return "DM_ENOENT";
   }
   return "DM_UNKNOWN";
 }
@@ -374,6 +457,11 @@ dm_status dm_merge_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_o
   if (st != DM_OK) return st;
   if (dm_scratch_bytes(in, flags) > ctx->arena_bytes) return DM_ENOMEM;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  if ((flags & DM_FLAG_AUTOTUNE) && needs_tuning(ctx, in)) {
+    st = dm_autotune_column(ctx, in, out, stream, flags, 0, nullptr);
+    if (st != DM_OK) return st;
+  }
+  flags &= ~DM_FLAG_AUTOTUNE;
   const bool timing = (flags & DM_FLAG_TIMING) != 0;
   if (timing && !ctx->ring) {
     ctx->ring = new (std::nothrow) cudaEvent_t[5 * dm_ctx::kRing]();
@@ -430,6 +518,17 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
   cudaStream_t s = as_stream(stream);
   ctx->timing_valid = false;
   if (ncols == 0) return DM_OK;
+  if (flags & DM_FLAG_AUTOTUNE) {
+    // each class once, on its first column (the graph below overwrites the
+    // outputs the tuning merges leave)
+    const uint32_t tf = flags & ~(DM_FLAG_AUTOTUNE | DM_FLAG_SERIAL | DM_FLAG_TIMING);
+    for (uint32_t c = 0; c < ncols; ++c) {
+      if (!needs_tuning(ctx, &in[c])) continue;
+      dm_status st = dm_autotune_column(ctx, &in[c], &out[c], stream, tf, 0, nullptr);
+      if (st != DM_OK) return st;
+    }
+    flags &= ~DM_FLAG_AUTOTUNE;
+  }
   if (flags & DM_FLAG_SERIAL) {
     // columns one after another on one stream, reusing one scratch region
     for (uint32_t c = 0; c < ncols; ++c) {
@@ -452,6 +551,9 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
   put(&ctx->arena, sizeof(ctx->arena));
   put(&ctx->tuning, sizeof(ctx->tuning));
   put(&ctx->coop_share, sizeof(ctx->coop_share));
+  const uint64_t tune_gen = dm_tune_cache_generation(ctx->tune_cache);
+  put(&ctx->tune_cache, sizeof(ctx->tune_cache));
+  put(&tune_gen, sizeof(tune_gen));
   for (uint32_t c = 0; c < ncols; ++c) {
     put(&in[c], sizeof(dm_column_in));
     put(&out[c], sizeof(dm_column_out));
@@ -472,16 +574,10 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
   std::vector<dm::ReencodePlan> plans(ncols);
   for (uint32_t c = 0; c < ncols; ++c) {
     if (in[c].main_rows + in[c].delta_rows == 0) continue;
-    dm::ReencodeArgs ra{};
-    ra.n_main = in[c].main_rows;
-    ra.n_delta = in[c].delta_rows;
-    ra.m = (uint32_t)std::min<uint64_t>(in[c].main_dict_len, 0xFFFFFFFFu);
-    ra.max_bits = bits_for(in[c].main_dict_len + in[c].delta_dict_len);
+    const Resolved rs = resolve(ctx, &in[c], flags, nullptr);
+    dm::ReencodeArgs ra = plan_args(&in[c], rs);
     ra.xdir = reinterpret_cast<uint32_t*>(16);   // a directory will exist
-    ra.tune_warps = ctx->tuning.reencode_warps;
-    ra.tune_stages = ctx->tuning.reencode_stages;
-    ra.tune_obufs = ctx->tuning.reencode_obufs;
-    if (dm::plan_reencode(in[c].main_bits, ra, ctx->sm_count, flags, &plans[c]) != cudaSuccess) return DM_ECUDA;
+    if (dm::plan_reencode(in[c].main_bits, ra, ctx->sm_count, rs.flags, &plans[c]) != cudaSuccess) return DM_ECUDA;
   }
   const uint64_t launches0 = ctx->launches;
   cudaGraph_t graph = nullptr;
@@ -762,6 +858,114 @@ dm_status dm_set_tuning(dm_ctx* ctx, const dm_tuning* t) {
 dm_status dm_get_tuning(const dm_ctx* ctx, dm_tuning* t) {
   if (!ctx || !t) return DM_EINVAL;
   *t = ctx->tuning;
+  return DM_OK;
+}
+
+dm_status dm_set_tune_cache(dm_ctx* ctx, dm_tune_cache* cache) {
+  if (!ctx) return DM_EINVAL;
+  ctx->tune_cache = cache ? cache : &ctx->own_cache;
+  return DM_OK;
+}
+
+dm_tune_cache* dm_get_tune_cache(dm_ctx* ctx) { return ctx ? ctx->tune_cache : nullptr; }
+
+uint32_t dm_tune_candidates(const dm_ctx* ctx, const dm_column_in* in, dm_tune_choice* out, uint32_t cap) {
+  if (!ctx || !in) return 0;
+  const std::vector<dm_tune_choice> v = tune_candidates(ctx, in);
+  for (uint32_t i = 0; i < cap && i < v.size() && out; ++i) out[i] = v[i];
+  return (uint32_t)v.size();
+}
+
+dm_status dm_autotune_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* stream,
+                             uint32_t flags, uint32_t reps, dm_tune_report* report) {
+  if (!ctx) return DM_EINVAL;
+  dm_status st = check_column(in, out, true);
+  if (st != DM_OK) return st;
+  if (dm_scratch_bytes(in, flags) > ctx->arena_bytes) return DM_ENOMEM;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  if (reps == 0) reps = 5;
+  if (reps > 1000) return DM_EINVAL;
+  flags &= ~(DM_FLAG_AUTOTUNE | DM_FLAG_SERIAL | DM_FLAG_TIMING | DM_FLAG_X_SMEM | DM_FLAG_X_GLOBAL);
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return DM_ECUDA;
+  }
+  uint32_t timed = 0;
+  // median of `reps` merges after one untimed merge
+  auto measure = [&](const dm_tune_choice& c, float* ms) -> dm_status {
+    std::vector<float> t;
+    for (uint32_t r = 0; r <= reps; ++r) {
+      if (cudaEventRecord(e0, s) != cudaSuccess) return DM_ECUDA;
+      dm_status rs = run_column(ctx, in, out, ctx->arena, s, flags, nullptr, nullptr, 0, nullptr, nullptr, &c);
+      if (rs != DM_OK) return rs;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return DM_ECUDA;
+      float x = 0;
+      if (r && cudaEventElapsedTime(&x, e0, e1) != cudaSuccess) return DM_ECUDA;
+      if (r) t.push_back(x);
+    }
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    ++timed;
+    return DM_OK;
+  };
+  const std::vector<dm_tune_choice> all = tune_candidates(ctx, in);
+  dm_tune_choice best{};
+  float best_ms = 0, default_ms = 0;
+  st = measure(best, &default_ms);
+  best_ms = default_ms;
+  std::vector<dm_tune_choice> tried = {best};   // each choice is timed once
+  // one axis at a time, each over the values the candidate list holds,
+  // the other fields held at the best so far
+  auto axis = [&](auto field) -> dm_status {
+    for (const dm_tune_choice& c : all) {
+      dm_tune_choice t = best;
+      field(t, c);
+      bool seen = false;
+      for (const auto& u : tried) seen = seen || memcmp(&u, &t, sizeof(t)) == 0;
+      if (seen) continue;
+      tried.push_back(t);
+      float ms = 0;
+      dm_status rs = measure(t, &ms);
+      if (rs != DM_OK) return rs;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+    return DM_OK;
+  };
+  if (st == DM_OK)
+    st = axis([](dm_tune_choice& t, const dm_tune_choice& c) {
+      t.x_staging = c.x_staging;
+      t.x8 = c.x8;
+    });
+  if (st == DM_OK)
+    st = axis([](dm_tune_choice& t, const dm_tune_choice& c) {
+      t.reencode_warps = c.reencode_warps;
+      t.reencode_stages = c.reencode_stages;
+      t.reencode_obufs = c.reencode_obufs;
+    });
+  if (st == DM_OK) st = axis([](dm_tune_choice& t, const dm_tune_choice& c) { t.step1_blocks = c.step1_blocks; });
+  // leave the result of the chosen launch in `out`
+  if (st == DM_OK) st = run_column(ctx, in, out, ctx->arena, s, flags, nullptr, nullptr, 0, nullptr, nullptr, &best);
+  if (st == DM_OK && cudaStreamSynchronize(s) != cudaSuccess) st = DM_ECUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DM_OK) return st;
+  const dm_tune_key key = dm::tune_key_of(*in);
+  st = dm_tune_cache_put(ctx->tune_cache, &key, &best);
+  if (st != DM_OK) return st;
+  if (report) {
+    *report = dm_tune_report{};
+    report->key = key;
+    report->best = best;
+    report->best_ms = best_ms;
+    report->default_ms = default_ms;
+    report->candidates = timed;
+    report->reps = reps;
+  }
   return DM_OK;
 }
 

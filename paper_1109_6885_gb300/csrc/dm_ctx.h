@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/dmerge.h"
+#include "dm_tune.h"
 
 struct dm_ctx {
   int device = 0;
@@ -31,6 +32,8 @@ struct dm_ctx {
   uint32_t ring_n = 0;
   cudaEvent_t* last_ev = nullptr;   // quadruple of the last timed call
   dm_tuning tuning{};
+  dm_tune_cache own_cache;                // launch choices per column class
+  dm_tune_cache* tune_cache = &own_cache; // or a cache shared with other contexts
   // batched table merges: side streams, fork/join events, graph cache
   static constexpr uint32_t kTableStreams = 4;
   cudaStream_t side[kTableStreams] = {};

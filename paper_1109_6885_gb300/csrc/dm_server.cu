@@ -37,6 +37,7 @@ struct dm_server {
     bool busy = false;
   };
   std::vector<Slot> slots;
+  dm_tune_cache tune_cache;   // shared by every slot's context
   struct Table {
     std::vector<dm_column_in> in;
     std::vector<dm_column_out> out;
@@ -133,11 +134,14 @@ dm_status dm_server_create(dm_server** out, int device, const dm_server_config* 
       return DM_ECUDA;
     }
     sl.ctx->coop_share = cfg->slots;
+    dm_set_tune_cache(sl.ctx, &S->tune_cache);
   }
   S->worker = std::thread(worker_main, S);
   *out = S;
   return DM_OK;
 }
+
+dm_tune_cache* dm_server_tune_cache(dm_server* S) { return S ? &S->tune_cache : nullptr; }
 
 void dm_server_destroy(dm_server* S) {
   if (!S) return;

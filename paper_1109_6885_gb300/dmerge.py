@@ -22,12 +22,16 @@ from . import build as _build
 _lib = None
 _lock = threading.Lock()
 
-DM_OK, DM_EINVAL, DM_ENOMEM, DM_EUNSORTED, DM_ECODE, DM_ECUDA, DM_ETIMEOUT, DM_EBUSY = range(8)
+(DM_OK, DM_EINVAL, DM_ENOMEM, DM_EUNSORTED, DM_ECODE, DM_ECUDA, DM_ETIMEOUT, DM_EBUSY,
+ DM_ENOENT) = range(9)
 DM_FLAG_GENERIC_REENCODE = 0x1
 DM_FLAG_X_SMEM = 0x2
 DM_FLAG_X_GLOBAL = 0x4
 DM_FLAG_TIMING = 0x8
 DM_FLAG_SERIAL = 0x10
+DM_FLAG_AUTOTUNE = 0x20
+DM_STAGE_AUTO, DM_STAGE_SMEM, DM_STAGE_GLOBAL = 0, 1, 2
+DM_X8_AUTO, DM_X8_OFF = 0, 1
 
 EXPORTS = [
     "dm_create", "dm_destroy", "dm_reserve", "dm_arena_bytes", "dm_packed_bytes", "dm_bits_for",
@@ -37,8 +41,12 @@ EXPORTS = [
     "dm_launch_count", "dm_merge_dicts_noalloc", "dm_set_tuning", "dm_get_tuning", "dm_last_error",
     "dm_server_create", "dm_server_destroy", "dm_server_add_table", "dm_server_submit",
     "dm_server_drain", "dm_server_request_info", "dm_server_stats_get", "dm_server_table_version",
-    "dm_sched_simulate",
+    "dm_sched_simulate", "dm_server_tune_cache",
     "dm_status_str",
+    "dm_tune_key_of", "dm_tune_cache_create", "dm_tune_cache_destroy", "dm_tune_cache_put",
+    "dm_tune_cache_get", "dm_tune_cache_size", "dm_tune_cache_generation", "dm_tune_cache_clear",
+    "dm_tune_cache_save", "dm_tune_cache_load", "dm_set_tune_cache", "dm_get_tune_cache",
+    "dm_tune_candidates", "dm_autotune_column",
 ]
 
 
@@ -71,6 +79,48 @@ class Tuning(ctypes.Structure):
         ("reencode_obufs", ctypes.c_uint32),
         ("host_chunks", ctypes.c_uint32),
         ("reserved", ctypes.c_uint32 * 4),
+    ]
+
+
+class TuneKey(ctypes.Structure):
+    _fields_ = [
+        ("value_bytes", ctypes.c_uint32),
+        ("main_bits", ctypes.c_uint32),
+        ("max_bits", ctypes.c_uint32),
+        ("log2_m", ctypes.c_uint32),
+        ("log2_d", ctypes.c_uint32),
+        ("log2_main_rows", ctypes.c_uint32),
+        ("log2_delta_rows", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+    def as_tuple(self):
+        return tuple(getattr(self, f) for f, _ in self._fields_[:-1])
+
+
+class TuneChoice(ctypes.Structure):
+    _fields_ = [
+        ("reencode_warps", ctypes.c_uint32),
+        ("reencode_stages", ctypes.c_uint32),
+        ("reencode_obufs", ctypes.c_uint32),
+        ("x_staging", ctypes.c_uint32),
+        ("x8", ctypes.c_uint32),
+        ("step1_blocks", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 2),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [
+        ("key", TuneKey),
+        ("best", TuneChoice),
+        ("best_ms", ctypes.c_float),
+        ("default_ms", ctypes.c_float),
+        ("candidates", ctypes.c_uint32),
+        ("reps", ctypes.c_uint32),
     ]
 
 
@@ -171,6 +221,21 @@ def _load():
             "dm_get_tuning": ([vp, ctypes.POINTER(Tuning)], i32),
             "dm_merge_dicts_noalloc": ([u32, vp, u64, vp, vp, u64, vp, vp, vp, vp, vp, vp, vp],
                                        i32),
+            "dm_server_tune_cache": ([vp], vp),
+            "dm_tune_key_of": ([pin, ctypes.POINTER(TuneKey)], i32),
+            "dm_tune_cache_create": ([ctypes.POINTER(vp)], i32),
+            "dm_tune_cache_destroy": ([vp], None),
+            "dm_tune_cache_put": ([vp, ctypes.POINTER(TuneKey), ctypes.POINTER(TuneChoice)], i32),
+            "dm_tune_cache_get": ([vp, ctypes.POINTER(TuneKey), ctypes.POINTER(TuneChoice)], i32),
+            "dm_tune_cache_size": ([vp], u64),
+            "dm_tune_cache_generation": ([vp], u64),
+            "dm_tune_cache_clear": ([vp], i32),
+            "dm_tune_cache_save": ([vp, ctypes.c_char_p], i32),
+            "dm_tune_cache_load": ([vp, ctypes.c_char_p], i32),
+            "dm_set_tune_cache": ([vp, vp], i32),
+            "dm_get_tune_cache": ([vp], vp),
+            "dm_tune_candidates": ([vp, pin, ctypes.POINTER(TuneChoice), u32], u32),
+            "dm_autotune_column": ([vp, pin, pout, vp, u32, u32, ctypes.POINTER(TuneReport)], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -231,8 +296,70 @@ def dm_table_scratch_bytes(cins, flags: int = 0) -> int:
     return int(_load().dm_table_scratch_bytes(arr, len(cins), flags))
 
 
+def dm_tune_key_of(cin: ColumnIn) -> TuneKey:
+    k = TuneKey()
+    _check(_load().dm_tune_key_of(ctypes.byref(cin), ctypes.byref(k)), "dm_tune_key_of")
+    return k
+
+
+class TuneCache:
+    """dm_tune_cache: launch choices per column class (host memory only).
+
+    Created with no handle it owns a new cache; given one (a context's or a
+    server's) it borrows it and `owner` keeps that owner alive."""
+
+    def __init__(self, handle=None, owner=None):
+        self._owned = handle is None
+        self.owner = owner
+        if handle is None:
+            h = ctypes.c_void_p()
+            _check(_load().dm_tune_cache_create(ctypes.byref(h)), "dm_tune_cache_create")
+            self.handle = h
+        else:
+            self.handle = ctypes.c_void_p(handle)
+
+    def close(self):
+        if self._owned and self.handle:
+            _load().dm_tune_cache_destroy(self.handle)
+        self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def put(self, key: TuneKey, choice: TuneChoice):
+        _check(_load().dm_tune_cache_put(self.handle, ctypes.byref(key), ctypes.byref(choice)),
+               "dm_tune_cache_put")
+
+    def get(self, key: TuneKey) -> TuneChoice | None:
+        c = TuneChoice()
+        rc = _load().dm_tune_cache_get(self.handle, ctypes.byref(key), ctypes.byref(c))
+        if rc == DM_ENOENT:
+            return None
+        _check(rc, "dm_tune_cache_get")
+        return c
+
+    def __len__(self) -> int:
+        return int(_load().dm_tune_cache_size(self.handle))
+
+    @property
+    def generation(self) -> int:
+        return int(_load().dm_tune_cache_generation(self.handle))
+
+    def clear(self):
+        _check(_load().dm_tune_cache_clear(self.handle), "dm_tune_cache_clear")
+
+    def save(self, path: str):
+        _check(_load().dm_tune_cache_save(self.handle, os.fsencode(path)), "dm_tune_cache_save")
+
+    def load(self, path: str):
+        _check(_load().dm_tune_cache_load(self.handle, os.fsencode(path)), "dm_tune_cache_load")
+
+
 class Context:
-    """Owns a dm_ctx (device, scratch arena, status word)."""
+    """Owns a dm_ctx (device, scratch arena, status word, tune cache)."""
 
     def __init__(self, device: int = 0, arena_bytes: int = 0):
         self.handle = ctypes.c_void_p()
@@ -277,6 +404,23 @@ class Context:
         _check(_load().dm_get_tuning(self.handle, ctypes.byref(t)), "dm_get_tuning")
         return t
 
+    @property
+    def tune_cache(self) -> TuneCache:
+        """The cache this context looks launch choices up in."""
+        return TuneCache(_load().dm_get_tune_cache(self.handle), owner=self)
+
+    def set_tune_cache(self, cache: TuneCache | None):
+        """Share `cache` (kept alive by this context); None: the context's own."""
+        _check(_load().dm_set_tune_cache(self.handle, cache.handle if cache else None),
+               "dm_set_tune_cache")
+        self._shared_cache = cache
+
+    def tune_candidates(self, cin: ColumnIn) -> list[TuneChoice]:
+        n = int(_load().dm_tune_candidates(self.handle, ctypes.byref(cin), None, 0))
+        arr = (TuneChoice * n)()
+        _load().dm_tune_candidates(self.handle, ctypes.byref(cin), arr, n)
+        return list(arr)
+
     def sync_status(self, stream=None) -> int:
         return int(_load().dm_sync_status(self.handle, _stream(stream)))
 
@@ -298,6 +442,15 @@ class Context:
 def dm_merge_column(ctx: Context, cin: ColumnIn, cout: ColumnOut, stream=None, flags: int = 0):
     _check(_load().dm_merge_column(ctx.handle, ctypes.byref(cin), ctypes.byref(cout),
                                    _stream(stream), flags), "dm_merge_column", ctx)
+
+
+def dm_autotune_column(ctx: Context, cin: ColumnIn, cout: ColumnOut, stream=None, flags: int = 0,
+                       reps: int = 0) -> TuneReport:
+    rep = TuneReport()
+    _check(_load().dm_autotune_column(ctx.handle, ctypes.byref(cin), ctypes.byref(cout),
+                                      _stream(stream), flags, reps, ctypes.byref(rep)),
+           "dm_autotune_column", ctx)
+    return rep
 
 
 def dm_merge_table(ctx: Context, cins, couts, stream=None, flags: int = 0):
@@ -519,6 +672,11 @@ class Server:
 
     def version(self, table_id: int) -> int:
         return int(_load().dm_server_table_version(self.handle, table_id))
+
+    @property
+    def tune_cache(self) -> TuneCache:
+        """The cache every slot looks its launch choices up in."""
+        return TuneCache(_load().dm_server_tune_cache(self.handle), owner=self)
 
 
 def dm_sched_simulate(pool_bytes: int, slots: int, footprint, service_ns, req_table, arrival_ns):
