@@ -506,6 +506,60 @@ dm_status record_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, cons
 
 }  // namespace
 
+namespace {
+
+// Median milliseconds of `reps` batched merges of a table (after one more
+// that records its graph), from CUDA events on the stream.
+dm_status time_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, const dm_column_out* out, void* stream,
+                     uint32_t flags, uint32_t reps, float* ms) {
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return DM_ECUDA;
+  }
+  std::vector<float> t;
+  dm_status st = DM_OK;
+  for (uint32_t r = 0; r <= reps && st == DM_OK; ++r) {
+    if (cudaEventRecord(e0, s) != cudaSuccess) st = DM_ECUDA;
+    if (st == DM_OK) st = dm_merge_table(ctx, in, ncols, out, stream, flags);
+    if (st == DM_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+      st = DM_ECUDA;
+    float x = 0;
+    if (st == DM_OK && r && cudaEventElapsedTime(&x, e0, e1) != cudaSuccess) st = DM_ECUDA;
+    if (st == DM_OK && r) t.push_back(x);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != DM_OK) return st;
+  std::sort(t.begin(), t.end());
+  *ms = t[t.size() / 2];
+  return DM_OK;
+}
+
+// The classes just tuned were timed one column at a time; inside the
+// table's graph columns run side by side, where another choice may win.
+// Keep their tuned choices only if the whole table runs faster with them
+// than with the library defaults; otherwise store the defaults for them
+// (so they are not tuned again).
+dm_status confirm_in_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, const dm_column_out* out,
+                           void* stream, uint32_t flags, const std::vector<dm_tune_key>& tuned) {
+  constexpr uint32_t kReps = 5;
+  std::vector<dm_tune_choice> chosen(tuned.size());
+  for (size_t i = 0; i < tuned.size(); ++i)
+    if (dm_tune_cache_get(ctx->tune_cache, &tuned[i], &chosen[i]) != DM_OK) return DM_EINVAL;
+  float with_tuned = 0, with_defaults = 0;
+  dm_status st = time_table(ctx, in, ncols, out, stream, flags, kReps, &with_tuned);
+  const dm_tune_choice defaults{};
+  for (size_t i = 0; i < tuned.size() && st == DM_OK; ++i) st = dm_tune_cache_put(ctx->tune_cache, &tuned[i], &defaults);
+  if (st == DM_OK) st = time_table(ctx, in, ncols, out, stream, flags, kReps, &with_defaults);
+  if (st != DM_OK || with_tuned < with_defaults)
+    for (size_t i = 0; i < tuned.size(); ++i) dm_tune_cache_put(ctx->tune_cache, &tuned[i], &chosen[i]);
+  return st;
+}
+
+}  // namespace
+
 dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, const dm_column_out* out,
                          void* stream, uint32_t flags) {
   if (!ctx || (ncols && (!in || !out))) return DM_EINVAL;
@@ -519,15 +573,21 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
   ctx->timing_valid = false;
   if (ncols == 0) return DM_OK;
   if (flags & DM_FLAG_AUTOTUNE) {
-    // each class once, on its first column (the graph below overwrites the
+    // each class once, on its first column (the merges below overwrite the
     // outputs the tuning merges leave)
     const uint32_t tf = flags & ~(DM_FLAG_AUTOTUNE | DM_FLAG_SERIAL | DM_FLAG_TIMING);
+    std::vector<dm_tune_key> tuned;
     for (uint32_t c = 0; c < ncols; ++c) {
       if (!needs_tuning(ctx, &in[c])) continue;
       dm_status st = dm_autotune_column(ctx, &in[c], &out[c], stream, tf, 0, nullptr);
       if (st != DM_OK) return st;
+      tuned.push_back(dm::tune_key_of(in[c]));
     }
     flags &= ~DM_FLAG_AUTOTUNE;
+    if (!tuned.empty() && !(flags & DM_FLAG_SERIAL)) {
+      dm_status st = confirm_in_table(ctx, in, ncols, out, stream, flags, tuned);
+      if (st != DM_OK) return st;
+    }
   }
   if (flags & DM_FLAG_SERIAL) {
     // columns one after another on one stream, reusing one scratch region

@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArg
           const uint32_t e = s_x[c[j] >> dshift];
           const uint32_t y = (c[j] & dmask) * (1u << 20) + e;   // multiply-add: FMA pipe
           x[j] = c[j] + (y & 0xFFFFFu) + __umulhi(y, 2u);        // y >> 31 on the FMA pipe
-          many |= ((e >> 21) == DIR_SLOW ? 1u : 0u) << j;
+          many |= (e < DIR_SLOW_BELOW ? 1u : 0u) << j;
         }
         // codes in buckets with several steps read X_M, or the byte table
         // where there is one (an X_M too large to stay in L2)

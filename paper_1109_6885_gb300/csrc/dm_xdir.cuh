@@ -11,7 +11,9 @@
 // For a code i with offset lo = i mod 2^s in its bucket, entry + (lo << 20)
 // carries into bit 31 exactly when lo >= thr, so
 //   X_M[i] = i + (y & 0xFFFFF) + (y >> 31),  y = entry + (lo << 20).
-// A bucket without steps stores thr = 2047 (never reached).  A bucket with
+// A bucket without steps stores thr = 1024 (above every offset, as s <= 10),
+// so that every entry of a bucket read through the lookup is at least
+// 1024 << 20 and the markers below are told apart by one compare.  A bucket with
 // two or more steps (up to 255) and a 20-bit base, when a byte table X8 of
 // c[i] - base exists, stores the marker thr = 2045 with its base, and its
 // codes read X8: X_M[i] = i + base + X8[i] (X8 is a quarter of X_M's size,
@@ -23,15 +25,18 @@
 
 namespace dm {
 
-constexpr uint32_t DIR_NONE = 2047, DIR_MANY = 2046, DIR_MANY8 = 2045;
+constexpr uint32_t DIR_NONE = 1024, DIR_MANY = 2046, DIR_MANY8 = 2045;
 constexpr uint32_t DIR_MANY_TOP = 2048 - DIR_MANY;     // top 12 bits of an entry read through X_M
 constexpr uint32_t DIR_MANY8_TOP = 2048 - DIR_MANY8;   // top 12 bits of an entry read through X8
-// Both markers share entry >> 21 == 1 (no other entry has it: NONE has top
-// 1, a single step top 1025..2048).
-constexpr uint32_t DIR_SLOW = DIR_MANY_TOP >> 1;
-static_assert((DIR_MANY8_TOP >> 1) == DIR_SLOW && (2048 - DIR_NONE) >> 1 != DIR_SLOW, "markers");
+// Entries of both markers are below DIR_SLOW_BELOW; every other entry is at
+// least 1024 << 20 (NONE has top 1024, a single step top 1025..2048).
+constexpr uint32_t DIR_SLOW_BELOW = 4u << 20;
+static_assert((DIR_MANY_TOP << 20) < DIR_SLOW_BELOW && (DIR_MANY8_TOP << 20) < DIR_SLOW_BELOW &&
+                  ((2048u - DIR_NONE) << 20) >= DIR_SLOW_BELOW,
+              "markers");
 constexpr uint32_t RE_DIR_MAX = 16384;               // entries (64 KiB of shared memory)
 constexpr uint32_t RE_DIR_SHIFT_MAX = 10;
+static_assert((1u << RE_DIR_SHIFT_MAX) <= DIR_NONE, "a bucket without steps never carries");
 
 // Entry of bucket b.  Coherent: X_M was written earlier in the same kernel,
 // so it is read through L2 (ld.global.cg), never from a stale L1 line.
