@@ -203,8 +203,9 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
  * path where cudaMalloc's implicit device-wide synchronisation (or its
  * failure when memory is fully reserved) is not acceptable.
  *
- * Its scratch (one look-back word per 2048-entry tile plus a tile counter,
- * at most 64 KiB) is a fixed array in the library's static device memory,
+ * Its scratch (one look-back word per merge tile of 4096 entries plus the
+ * barrier and tile counters; the array is sized for tiles of 2048, 64 KiB
+ * and 128 bytes) is a fixed array in the library's static device memory,
  * so every GPU that loads libdmerge holds those 64 KiB until the process
  * exits.  The first call on a device looks the array's device address up
  * (cudaGetSymbolAddress, with that device current); make that first call
