@@ -67,6 +67,13 @@ SERVES = {
                                      requests=200, slots=4, budget=16 << 30),
     "serve-16tables-burst": dict(ntables=16, cols=(20, 60), rows=(100_000, 4_000_000), rate=0.0,
                                  requests=200, slots=4, budget=16 << 30),
+    # the served configuration's shape: 64 tables of 20-200 columns, main rows
+    # log-uniform in [100k, 200M], delta 0.1-10%, Poisson 20 requests/s, 150 GB
+    # admission budget.  Distinct data for all ~7,000 columns would need about
+    # 0.5 TB, beyond HBM, so a table's columns repeat `distinct` column data
+    # sets (inputs and outputs; repeats write identical bytes)
+    "serve-64tables-poisson20": dict(ntables=64, cols=(20, 200), rows=(100_000, 200_000_000), rate=20.0,
+                                     requests=400, slots=4, budget=150 << 30, distinct=2),
 }
 DEFAULT_WORKLOAD = "column-100M-u64-zipf1-delta1M"
 L2_BYTES = 129 * 2**20
@@ -580,7 +587,9 @@ def run_table(args):
 
 
 def run_serve(args):
-    """Served merges: Poisson (or burst) arrivals of table merges, continuous batching."""
+    """Served merges: Poisson (or burst) arrivals of table merges, continuous
+    batching; the same arrivals again through a plain arm (one table at a
+    time, per-column plain launches)."""
     import torch
 
     from paper_1109_6885_gb300 import build
@@ -592,72 +601,94 @@ def run_serve(args):
     dm.load()
     cfg = SERVES[args.workload]
     rng = np.random.default_rng(0x5E7E + rank)
-    srv = dm.Server(local, slots=cfg["slots"], scratch_budget=cfg["budget"])
-    keep = []
+    keep, tables = [], []
     for t in range(cfg["ntables"]):
         ncols = int(rng.integers(cfg["cols"][0], cfg["cols"][1] + 1))
         n_main = int(np.exp(rng.uniform(np.log(cfg["rows"][0]), np.log(cfg["rows"][1]))))
         n_delta = max(1, int(n_main * np.exp(rng.uniform(np.log(0.001), np.log(0.1)))))
+        nsrc = min(ncols, cfg.get("distinct", ncols))
         cins, couts = [], []
         for j in range(ncols):
             m = int(np.exp(rng.uniform(np.log(2), np.log(n_main))))
             spec = synth.ColumnSpec(n_main=n_main, m=m, w=int(rng.choice([4, 8, 16])), n_delta=n_delta,
                                     f_new=float(rng.uniform(0, 0.5)), dist="zipf", zipf_s=0.8,
                                     seed=synth.column_seed(5 + 1000 * rank + t, j))
-            c = synth.make_column(spec)
-            d = dm.DeviceColumn.from_numpy(c.w, c.main_dict, c.main_packed, c.main_bits, c.n_main,
-                                           c.delta_dict, c.delta_codes)
-            r = dm.alloc_result(d, with_x=False)
-            keep.append((d, r))
-            cins.append(d.cin())
-            couts.append(r.cout())
-        srv.add_table(t, cins, couts)
-    # warm-up: one merge of every table (records their graphs)
-    for t in range(cfg["ntables"]):
-        srv.submit(t)
-    srv.drain()
-    base = srv.stats()
+            if j < nsrc:
+                c = synth.make_column(spec)
+                d = dm.DeviceColumn.from_numpy(c.w, c.main_dict, c.main_packed, c.main_bits, c.n_main,
+                                               c.delta_dict, c.delta_codes)
+                r = dm.alloc_result(d, with_x=False)
+                keep.append((d, r))
+                cins.append(d.cin())
+                couts.append(r.cout())
+                del c
+            else:
+                cins.append(cins[j % nsrc])
+                couts.append(couts[j % nsrc])
+        tables.append((cins, couts))
     nreq = max(args.steps * 10, cfg["requests"])
     tabs = rng.integers(0, cfg["ntables"], nreq)
     gaps = rng.exponential(1.0 / cfg["rate"], nreq) if cfg["rate"] > 0 else np.zeros(nreq)
-    sampler = ClockSampler(local, not args.no_clocks)
-    sampler.wait_ready()
-    t0 = time.perf_counter()
-    due = t0
-    for t, g in zip(tabs, gaps):
-        due += g
-        while True:
-            now = time.perf_counter()
-            if now >= due:
-                break
-            time.sleep(min(due - now, 0.002))
-        srv.submit(int(t))
-    srv.drain()
-    wall = time.perf_counter() - t0
-    clocks = sampler.stop()
-    st = srv.stats()
-    # latency over the timed requests only
-    lat = []
-    for rid in range(base.submitted, st.submitted):
-        info = srv.info(rid)
-        lat.append((info.done_ns - info.submit_ns) / 1e6)
-    lat.sort()
-    tuples = st.tuples - base.tuples
+
+    def arm(slots, flags, clocks_on):
+        srv = dm.Server(local, slots=slots, scratch_budget=cfg["budget"], flags=flags)
+        for t, (cins, couts) in enumerate(tables):
+            srv.add_table(t, cins, couts)
+        # warm-up: one merge of every table (records their graphs)
+        for t in range(cfg["ntables"]):
+            srv.submit(t)
+        srv.drain()
+        base = srv.stats()
+        sampler = ClockSampler(local, clocks_on)
+        sampler.wait_ready()
+        t0 = time.perf_counter()
+        due = t0
+        for t, g in zip(tabs, gaps):
+            due += g
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                time.sleep(min(due - now, 0.002))
+            srv.submit(int(t))
+        srv.drain()
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop()
+        st = srv.stats()
+        # latency over the timed requests only
+        lat = []
+        for rid in range(base.submitted, st.submitted):
+            info = srv.info(rid)
+            lat.append((info.done_ns - info.submit_ns) / 1e6)
+        lat.sort()
+        out = {"value": (st.tuples - base.tuples) / wall, "wall_s": wall,
+               "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                              "max": lat[-1]},
+               "failed": st.failed - base.failed, "peak_concurrency": st.peak_concurrency,
+               "peak_scratch_bytes": st.peak_scratch_bytes, "scratch_budget": st.scratch_budget,
+               "clocks": clocks}
+        srv.close()
+        return out
+
+    served = arm(cfg["slots"], 0, not args.no_clocks)
+    plain = arm(1, dm.DM_FLAG_SERIAL, False)
     if rank == 0:
         line = {
-            "metric": "served merged tuple-columns/s; p50/p99 merge latency", "value": tuples / wall,
+            "metric": "served merged tuple-columns/s; p50/p99 merge latency", "value": served["value"],
             "unit": "tuple-columns/s", "n_gpus": world, "steps": nreq, "warmup": cfg["ntables"],
-            "ms_per_step": 1e3 * wall / nreq, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * served["wall_s"] / nreq, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "mixed u32/u64/u128", "data": "synthetic",
-            "config": {"workload": args.workload, **{k: v for k, v in cfg.items()}},
-            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                           "max": lat[-1]},
-            "requests": nreq, "failed": st.failed - base.failed,
-            "peak_concurrency": st.peak_concurrency, "peak_scratch_bytes": st.peak_scratch_bytes,
-            "scratch_budget": st.scratch_budget, "clocks": clocks,
+            "config": {"workload": args.workload, **{k: v for k, v in cfg.items()},
+                       "columns": sum(len(c) for c, _ in tables),
+                       "tuples_per_merge_mean": float(np.mean([sum(ci.main_rows + ci.delta_rows for ci in c)
+                                                               for c, _ in tables]))},
+            "latency_ms": served["latency_ms"], "requests": nreq, "failed": served["failed"],
+            "peak_concurrency": served["peak_concurrency"], "peak_scratch_bytes": served["peak_scratch_bytes"],
+            "scratch_budget": served["scratch_budget"], "clocks": served["clocks"],
+            "plain": {"form": "one table at a time, per-column plain launches, same arrivals",
+                      "value": plain["value"], "latency_ms": plain["latency_ms"], "failed": plain["failed"]},
         }
         print(json.dumps(line), flush=True)
-    srv.close()
 
 
 def main():

@@ -101,6 +101,7 @@ struct SortSmem {
   uint32_t wsum[S1_WARPS];
   K keys[SR_TILE];                 // the tile in digit order
   uint32_t vals[SR_TILE];
+  uint32_t next;                   // split form: the tile a block takes next
 };
 
 template <int W>
@@ -1023,6 +1024,150 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
   }
 }
 
+// ---------------------------------------------------------------- split form
+// When a launch may hold only a few blocks (several merges share the GPU,
+// each cooperative grid capped so that all of them fit at once) and the
+// merge has more tiles than that, the merge leaves the cooperative kernel:
+// the kernel sorts (or does nothing), then the kernels below find every
+// tile boundary, merge the tiles on as many blocks as the device holds, and
+// build the X_M directory.  The merge needs no co-residency: each block
+// takes its next tile from a counter, so a tile's look-back only waits on
+// tiles that running blocks have already taken.
+
+// The sort in the same spirit, for a delta dictionary too large for a capped
+// grid: one kernel per step, every block deriving the plan from the global
+// histogram, tiles of a pass taken from a per-pass counter (barriers[p]),
+// so that a pass's look-back only waits on tiles already taken.  A pass over
+// a byte the plan skips, or the passes when the plan partitions on the top
+// byte instead (and the reverse), return at once.
+
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS, 2) step1_hist_kernel(Step1Args a) {
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
+  hist_phase<W>(a, U.hist);
+}
+
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS, 2) step1_pass_kernel(Step1Args a, int pass) {
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
+  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(Step1Smem<W>) + 15) / 16 * 16);
+  bool msd = false;
+  const uint32_t run = plan_phase<W>(a, U.sp.plan, s_wsum, &msd);
+  if (msd || !((run >> pass) & 1u)) return;
+  const int e = __popc(run & ((1u << pass) - 1u));
+  for (;;) {
+    if (threadIdx.x == 0) U.sp.s.next = atomicAdd(a.barriers + pass, 1u);
+    __syncthreads();
+    const uint32_t t = U.sp.s.next;
+    __syncthreads();
+    if (t >= a.sort_tiles) break;
+    pass_tile<W>(a, pass, t, e, U.sp.plan, U.sp.s);
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS, 2) step1_msd_kernel(Step1Args a) {
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
+  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(Step1Smem<W>) + 15) / 16 * 16);
+  bool msd = false;
+  const uint32_t run = plan_phase<W>(a, U.sp.plan, s_wsum, &msd);
+  if (!msd) return;
+  const int top = 31 - __clz(run);
+  for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) msd_tile<W>(a, top, t, U.sp.plan, U.sp.s);
+}
+
+// The buckets of the top-byte partition, each sorted in shared memory; and
+// where the sorted keys are, for the merge.
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS, 2) step1_bucket_kernel(Step1Args a) {
+  using K = typename KeyOf<W>::T;
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
+  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(Step1Smem<W>) + 15) / 16 * 16);
+  bool msd = false;
+  const uint32_t run = plan_phase<W>(a, U.sp.plan, s_wsum, &msd);
+  K* k0 = static_cast<K*>(a.keys[0]);
+  uint32_t* v0 = a.vals[0];
+  if (msd) {
+    const int top = 31 - __clz(run);
+    const uint32_t lower = run & ((1u << top) - 1u);
+    const int sub = lower ? 31 - __clz(lower) : -1;
+    for (uint32_t b = blockIdx.x; b < 256; b += gridDim.x) {
+      const uint32_t off = U.sp.plan[top * 256 + b];
+      const uint32_t n = (b < 255 ? U.sp.plan[top * 256 + b + 1] : (uint32_t)a.d) - off;
+      if (n <= 1) continue;
+      if (sub >= 0) bucket_sort_sub<W>(k0, v0, off, n, true, k0, v0, sub, U.bp.b);
+      else bucket_sort<W>(k0, v0, off, n, true, k0, v0, U.bp.b);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const bool last_odd = !msd && ((__popc(run) - 1) & 1);
+    a.final_slot[0] = last_odd ? a.keys[1] : a.keys[0];
+    a.final_slot[1] = last_odd ? a.vals[1] : a.vals[0];
+  }
+}
+
+// U_D and perm for a merge that follows the sorting launch, or the caller's.
+template <int W>
+__device__ __forceinline__ void sorted_delta(const Step1Args& a, const typename KeyOf<W>::T** ud, const uint32_t** up) {
+  using K = typename KeyOf<W>::T;
+  if ((a.phases & S1_SORT) && a.d > 0) {
+    *ud = static_cast<const K*>(a.final_slot[0]);
+    *up = static_cast<const uint32_t*>(a.final_slot[1]);
+  } else {
+    *ud = static_cast<const K*>(a.b);
+    *up = a.perm;
+  }
+}
+
+// U_M co-rank of every tile boundary, one warp each.
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS) step1_cut_kernel(Step1Args a) {
+  using K = typename KeyOf<W>::T;
+  const K* ud;
+  const uint32_t* up;
+  sorted_delta<W>(a, &ud, &up);
+  constexpr uint32_t T = MergeSmem<W>::T;
+  const uint64_t n = a.m + a.d;
+  const uint32_t nwt = gridDim.x * S1_WARPS;
+  for (uint32_t b = blockIdx.x * S1_WARPS + (threadIdx.x >> 5); b <= a.merge_tiles; b += nwt) {
+    const uint64_t k = (uint64_t)b * T < n ? (uint64_t)b * T : n;
+    const uint64_t c = corank_warp(static_cast<const K*>(a.a), a.m, ud, a.d, k, false);
+    if ((threadIdx.x & 31) == 0) a.cuts[b] = c;
+  }
+}
+
+// The merge tiles, each block taking the next from a counter.
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS, 2) step1_merge_kernel(Step1Args a) {
+  using K = typename KeyOf<W>::T;
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
+  const K* ud;
+  const uint32_t* up;
+  sorted_delta<W>(a, &ud, &up);
+  uint32_t* next = a.barriers + S1_BARRIERS - 1;
+  for (;;) {
+    if (threadIdx.x == 0) U.m.next_tile = atomicAdd(next, 1u);
+    __syncthreads();
+    const uint32_t t = U.m.next_tile;
+    if (t >= a.merge_tiles) break;
+    merge_tile<W>(a, t, ud, up, false, true, U.m);
+  }
+}
+
+// The X_M directory (and its byte table) from the finished X_M.
+__global__ void __launch_bounds__(S1_THREADS) step1_dir_kernel(Step1Args a) {
+  const uint32_t t = blockIdx.x * S1_THREADS + threadIdx.x, nt = gridDim.x * S1_THREADS;
+  for (uint32_t b = t; b < a.dir_entries; b += nt)
+    a.xdir[b] = xdir_entry<false>(a.xm, (uint32_t)a.m, a.dir_shift, b, a.x8 != nullptr);
+  if (a.x8)
+    for (uint32_t i = t; i < a.m; i += nt) a.x8[i] = xdir_x8<false>(a.xm, a.dir_shift, i);
+}
+
 template <int W>
 __global__ void sort_copy_kernel(void* const* slot, uint64_t d, typename KeyOf<W>::T* keys_out, uint32_t* perm_out) {
   using K = typename KeyOf<W>::T;
@@ -1052,6 +1197,10 @@ cudaError_t prepare_w() {
   if (L.ready[wi]) return cudaSuccess;
   const size_t smem = step1_smem_bytes<W>();
   cudaError_t e = cudaFuncSetAttribute(step1_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  for (const void* fn : {(const void*)step1_merge_kernel<W>, (const void*)step1_hist_kernel<W>,
+                         (const void*)step1_pass_kernel<W>, (const void*)step1_msd_kernel<W>,
+                         (const void*)step1_bucket_kernel<W>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.per_sm[wi], step1_kernel<W>, S1_THREADS, smem);
   if (e != cudaSuccess) return e;
@@ -1073,31 +1222,71 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
     per_sm = L.per_sm[wi];
   }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  // all blocks resident at once (cooperative launch); no more blocks than
-  // the largest phase has tiles
-  uint64_t want = 1;
-  if ((a.phases & S1_SORT) && a.d > BK_SINGLE) want = std::max<uint64_t>(want, std::max<uint64_t>(a.sort_tiles, 256));
-  if (a.phases & S1_MERGE) want = std::max<uint64_t>(want, a.merge_tiles);
-  if (a.phases & S1_DIR) want = std::max<uint64_t>(want, (a.dir_entries + S1_THREADS - 1) / S1_THREADS);
-  uint64_t cap = (uint64_t)per_sm * sm_count;
+  const uint64_t full = (uint64_t)per_sm * sm_count;
+  uint64_t cap = full;
   if (a.grid_cap && a.grid_cap < cap) cap = a.grid_cap;
-  const uint32_t grid = (uint32_t)std::min(want, cap);
-  a.hist_blocks = (uint32_t)std::min<uint64_t>(
-      grid, std::max<uint64_t>(1, (a.d + S1_THREADS * HI_ITEMS - 1) / (S1_THREADS * HI_ITEMS)));
+  // a capped grid with fewer blocks than the merge has tiles, or than a
+  // quarter of the sort's: the split form (a split sort implies a split merge,
+  // which finds the sorted keys where the sort left them)
+  const bool capped = cap < full && a.final_slot != nullptr;
+  const bool split_sort = capped && (a.phases & S1_SORT) && a.d > BK_SINGLE && a.sort_tiles > 4 * cap;
+  const bool split = capped && (a.phases & S1_MERGE) && a.m + a.d > 0 && a.cuts != nullptr &&
+                     (a.merge_tiles > cap || split_sort);
+  Step1Args c = a;
+  if (split) c.phases &= S1_SORT;
+  if (split_sort) c.phases = 0;
+  cudaError_t e = cudaSuccess;
+  if (c.phases && !(c.phases == S1_SORT && a.d == 0)) {
+    // all blocks resident at once (cooperative launch); no more blocks than
+    // the largest phase has tiles
+    uint64_t want = 1;
+    if ((c.phases & S1_SORT) && c.d > BK_SINGLE) want = std::max<uint64_t>(want, std::max<uint64_t>(c.sort_tiles, 256));
+    if (c.phases & S1_MERGE) want = std::max<uint64_t>(want, c.merge_tiles);
+    if (c.phases & S1_DIR) want = std::max<uint64_t>(want, (c.dir_entries + S1_THREADS - 1) / S1_THREADS);
+    const uint32_t grid = (uint32_t)std::min(want, cap);
+    c.hist_blocks = (uint32_t)std::min<uint64_t>(
+        grid, std::max<uint64_t>(1, (c.d + S1_THREADS * HI_ITEMS - 1) / (S1_THREADS * HI_ITEMS)));
 
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(S1_THREADS);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, step1_kernel<W>, a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(S1_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, step1_kernel<W>, c);
+    ++*launches;
+  }
+  if (e != cudaSuccess) return e;
+  if (split_sort) {
+    Step1Args h = a;
+    h.hist_blocks = (uint32_t)std::min<uint64_t>(full, (a.d + S1_THREADS * HI_ITEMS - 1) / (S1_THREADS * HI_ITEMS));
+    step1_hist_kernel<W><<<h.hist_blocks, S1_THREADS, smem, s>>>(h);
+    ++*launches;
+    const uint32_t sort_grid = (uint32_t)std::min<uint64_t>(full, a.sort_tiles);
+    for (int p = 0; p < W; ++p) {
+      step1_pass_kernel<W><<<sort_grid, S1_THREADS, smem, s>>>(a, p);
+      ++*launches;
+    }
+    step1_msd_kernel<W><<<sort_grid, S1_THREADS, smem, s>>>(a);
+    step1_bucket_kernel<W><<<(uint32_t)std::min<uint64_t>(full, 256), S1_THREADS, smem, s>>>(a);
+    *launches += 2;
+  }
+  if (!split) return cudaGetLastError();
+  const uint32_t cut_blocks = (uint32_t)std::min<uint64_t>(full, (a.merge_tiles + S1_WARPS) / S1_WARPS);
+  step1_cut_kernel<W><<<cut_blocks, S1_THREADS, 0, s>>>(a);
   ++*launches;
-  return e;
+  step1_merge_kernel<W><<<(uint32_t)std::min<uint64_t>(full, a.merge_tiles), S1_THREADS, smem, s>>>(a);
+  ++*launches;
+  if ((a.phases & S1_DIR) && a.dir_entries > 0) {
+    const uint64_t work = std::max<uint64_t>(a.dir_entries, a.x8 ? a.m : 0);
+    step1_dir_kernel<<<(uint32_t)std::min<uint64_t>(4096, (work + S1_THREADS - 1) / S1_THREADS), S1_THREADS, 0, s>>>(a);
+    ++*launches;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace

@@ -270,3 +270,46 @@ def test_server_slots_share_one_cache(built):
     for ref, r, c in zip(refs, results, cols):
         ref.check(r, c.w)
     srv.close()
+
+
+# Step 1 under a capped grid: the merge (and, for a large delta dictionary,
+# the sort) leave the cooperative kernel for kernels that take tiles from a
+# counter.  Delta dictionaries of ~200k uniform keys partition on their top
+# byte; ~750k+ keys overflow its buckets and take the byte-by-byte passes.
+SPLIT_CASES = {
+    "msd": dict(n_main=2_000_003, m=300_000, n_delta=400_001, f_new=0.5, dist="zipf", zipf_s=0.8),
+    "lsd": dict(n_main=1_000_003, m=1_000_000, n_delta=1_500_001, f_new=0.5, dist="uniform"),
+}
+
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+@pytest.mark.parametrize("case", list(SPLIT_CASES))
+def test_capped_step1_split_forms(built, w, case):
+    import torch
+    spec = synth.ColumnSpec(w=w, seed=synth.column_seed(11, w + len(case)), **SPLIT_CASES[case])
+    col = synth.make_column(spec)
+    if case == "lsd":
+        assert col.delta_dict.shape[0] > 256 * 2048   # the top byte's buckets overflow
+    ref = DeviceRef(col)
+    ctx = dm.Context(0, 0)
+    dcol = _device_column(col)
+    cin = dcol.cin()
+    ctx.reserve(dm.dm_scratch_bytes(cin))
+    res = dm.alloc_result(dcol)
+    key = dm.dm_tune_key_of(cin)
+    for blocks in (1, 8, 38):
+        ctx.tune_cache.put(key, choice_of(step1_blocks=blocks))
+        for _ in range(2):
+            _fill_junk(res)
+            dm.dm_merge_column(ctx, cin, res.cout())
+            torch.cuda.synchronize()
+            assert ctx.sync_status() == dm.DM_OK, blocks
+            ref.check(res, col.w)
+    ctx.close()
+
+
+def choice_of(**kw):
+    c = dm.TuneChoice()
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
