@@ -92,6 +92,11 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--no-autotune", action="store_true",
                    help="table workloads: run on the library defaults instead of tuned launch choices")
+    p.add_argument("--serve-slots", default=None,
+                   help="served workloads: comma-separated slot counts, each timed on the same arrivals "
+                        "(the first is the line's value; default: the workload's)")
+    p.add_argument("--serve-flags", type=int, default=None,
+                   help="served workloads: dm_merge_table flags of the served arm (default: the workload's)")
     p.add_argument("--tune-cache", default=None,
                    help="table workloads: load tuned choices from this JSON file first, save them after")
     return p.parse_args()
@@ -626,6 +631,7 @@ def run_serve(args):
                 cins.append(cins[j % nsrc])
                 couts.append(couts[j % nsrc])
         tables.append((cins, couts))
+    table_tuples = [int(sum(ci.main_rows + ci.delta_rows for ci in c)) for c, _ in tables]
     nreq = max(args.steps * 10, cfg["requests"])
     tabs = rng.integers(0, cfg["ntables"], nreq)
     gaps = rng.exponential(1.0 / cfg["rate"], nreq) if cfg["rate"] > 0 else np.zeros(nreq)
@@ -656,21 +662,32 @@ def run_serve(args):
         clocks = sampler.stop()
         st = srv.stats()
         # latency over the timed requests only
-        lat = []
+        lat, per = [], []
         for rid in range(base.submitted, st.submitted):
             info = srv.info(rid)
             lat.append((info.done_ns - info.submit_ns) / 1e6)
+            per.append((lat[-1], int(info.table_id), (info.admit_ns - info.submit_ns) / 1e6))
         lat.sort()
+        per.sort(reverse=True)
+        slowest = [{"table": t, "tuples": table_tuples[t], "ms": round(ms, 3), "queued_ms": round(q, 3)}
+                   for ms, t, q in per[:5]]
         out = {"value": (st.tuples - base.tuples) / wall, "wall_s": wall,
                "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                               "max": lat[-1]},
                "failed": st.failed - base.failed, "peak_concurrency": st.peak_concurrency,
                "peak_scratch_bytes": st.peak_scratch_bytes, "scratch_budget": st.scratch_budget,
-               "clocks": clocks}
+               "clocks": clocks, "slowest": slowest}
         srv.close()
         return out
 
-    served = arm(cfg["slots"], 0, not args.no_clocks)
+    served_flags = cfg.get("flags", 0) if args.serve_flags is None else args.serve_flags
+    slot_counts = [int(x) for x in args.serve_slots.split(",")] if args.serve_slots else [cfg["slots"]]
+    served = arm(slot_counts[0], served_flags, not args.no_clocks)
+    sweep = []
+    for k in slot_counts[1:]:
+        r = arm(k, served_flags, False)
+        sweep.append({"slots": k, "value": r["value"], "latency_ms": r["latency_ms"], "failed": r["failed"],
+                      "peak_concurrency": r["peak_concurrency"]})
     plain = arm(1, dm.DM_FLAG_SERIAL, False)
     if rank == 0:
         line = {
@@ -685,8 +702,11 @@ def run_serve(args):
             "latency_ms": served["latency_ms"], "requests": nreq, "failed": served["failed"],
             "peak_concurrency": served["peak_concurrency"], "peak_scratch_bytes": served["peak_scratch_bytes"],
             "scratch_budget": served["scratch_budget"], "clocks": served["clocks"],
+            "slots": slot_counts[0], "served_flags": served_flags, "slowest": served["slowest"],
             "plain": {"form": "one table at a time, per-column plain launches, same arrivals",
-                      "value": plain["value"], "latency_ms": plain["latency_ms"], "failed": plain["failed"]},
+                      "value": plain["value"], "latency_ms": plain["latency_ms"], "failed": plain["failed"],
+                      "slowest": plain["slowest"]},
+            **({"slots_sweep": sweep} if sweep else {}),
         }
         print(json.dumps(line), flush=True)
 

@@ -80,6 +80,9 @@ typedef enum {
 #define DM_FLAG_X_GLOBAL 0x4u          /* never stage X_M in shared memory */
 #define DM_FLAG_TIMING 0x8u            /* record per-step CUDA events (dm_last_timing) */
 #define DM_FLAG_SERIAL 0x10u           /* dm_merge_table: one column after another, plain launches */
+#define DM_FLAG_NO_GRAPH 0x40u         /* dm_merge_table: the batched schedule issued directly on the
+                                          branches' streams, not recorded into a graph (for callers
+                                          whose buffers or scratch move between calls) */
 #define DM_FLAG_AUTOTUNE 0x20u         /* dm_merge_column / dm_merge_table: first tune every column
                                           class missing from the tune cache (dm_autotune_column;
                                           blocks the host while it runs) */
@@ -235,8 +238,11 @@ dm_status dm_merge_dicts_noalloc(uint32_t value_bytes, const void* main_dict, ui
  * thread watches completions, commits each table's new version (the
  * registry's pointer swap of the paper's atomic commit, Section 3), frees
  * the region and admits the next requests, so work that arrives while
- * other merges run joins them on the device.  Results land in the output
- * buffers given at registration; a table serves one merge at a time. */
+ * other merges run joins them on the device.  Each merge is launched on a
+ * stream whose priority follows its size (fewer tuples, higher priority),
+ * so a small merge that joins a large one is not held behind its kernels.
+ * Results land in the output buffers given at registration; a table serves
+ * one merge at a time. */
 typedef struct dm_server dm_server;
 
 typedef struct {

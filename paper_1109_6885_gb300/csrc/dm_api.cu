@@ -482,7 +482,23 @@ dm_status dm_merge_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_o
 
 namespace {
 
-// Record the batched schedule of a table on `s` (already capturing): columns
+// Launch plans of a table's Step 2(b) kernels, made before any launch (their
+// attribute and occupancy queries must stay out of a stream capture).
+bool plan_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, uint32_t flags,
+                std::vector<dm::ReencodePlan>* plans) {
+  if (dm::step1_prepare() != cudaSuccess) return false;
+  plans->assign(ncols, dm::ReencodePlan{});
+  for (uint32_t c = 0; c < ncols; ++c) {
+    if (in[c].main_rows + in[c].delta_rows == 0) continue;
+    const Resolved rs = resolve(ctx, &in[c], flags, nullptr);
+    dm::ReencodeArgs ra = plan_args(&in[c], rs);
+    ra.xdir = reinterpret_cast<uint32_t*>(16);   // a directory will exist
+    if (dm::plan_reencode(in[c].main_bits, ra, ctx->sm_count, rs.flags, &(*plans)[c]) != cudaSuccess) return false;
+  }
+  return true;
+}
+
+// Record the batched schedule of a table on `s` (capturing, or live): columns
 // round-robin over the side streams, each stream with its own scratch.
 dm_status record_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, const dm_column_out* out,
                        cudaStream_t s, uint32_t flags, const std::vector<dm::ReencodePlan>& plans, uint32_t S,
@@ -603,6 +619,12 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
   const uint32_t S = std::min<uint32_t>(ncols, dm_ctx::kTableStreams);
   size_t region = 0;
   for (uint32_t c = 0; c < ncols; ++c) region = std::max(region, align_up(dm_scratch_bytes(&in[c], flags)));
+  if (flags & DM_FLAG_NO_GRAPH) {
+    // the same schedule, issued on the branches' streams directly
+    std::vector<dm::ReencodePlan> plans;
+    if (!plan_table(ctx, in, ncols, flags, &plans)) return DM_ECUDA;
+    return record_table(ctx, in, ncols, out, s, flags, plans, S, region);
+  }
   std::string key;
   key.reserve(64 + ncols * (sizeof(dm_column_in) + sizeof(dm_column_out)));
   auto put = [&key](const void* p, size_t n) { key.append(static_cast<const char*>(p), n); };
@@ -630,15 +652,8 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
   }
   // plan every launch before recording (attribute and occupancy queries
   // stay out of the capture)
-  if (dm::step1_prepare() != cudaSuccess) return DM_ECUDA;
-  std::vector<dm::ReencodePlan> plans(ncols);
-  for (uint32_t c = 0; c < ncols; ++c) {
-    if (in[c].main_rows + in[c].delta_rows == 0) continue;
-    const Resolved rs = resolve(ctx, &in[c], flags, nullptr);
-    dm::ReencodeArgs ra = plan_args(&in[c], rs);
-    ra.xdir = reinterpret_cast<uint32_t*>(16);   // a directory will exist
-    if (dm::plan_reencode(in[c].main_bits, ra, ctx->sm_count, rs.flags, &plans[c]) != cudaSuccess) return DM_ECUDA;
-  }
+  std::vector<dm::ReencodePlan> plans;
+  if (!plan_table(ctx, in, ncols, flags, &plans)) return DM_ECUDA;
   const uint64_t launches0 = ctx->launches;
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeRelaxed);

@@ -13,6 +13,7 @@
 // run join as soon as resources allow and overlap them on the device.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <mutex>
@@ -29,9 +30,16 @@ struct dm_server {
   dm_server_config cfg{};
   void* pool = nullptr;
   dm::Scheduler* sched = nullptr;
+  // Streams of every priority the device offers, per slot: a table merge is
+  // launched at a priority set by its size (fewer tuples: higher), so that
+  // small merges admitted next to a large one are not queued behind its
+  // kernels at block granularity.
+  static constexpr int kLevels = 8;
+  int levels = 1, greatest = 0;
   struct Slot {
     dm_ctx* ctx = nullptr;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;            // the stream of the merge in flight
+    cudaStream_t by_level[kLevels] = {};      // [0]: highest priority
     cudaEvent_t done = nullptr;
     uint64_t req = 0;
     bool busy = false;
@@ -58,6 +66,14 @@ struct dm_server {
 
 namespace {
 
+// Priority level of a merge of `tuples` tuples: 0 (highest) below 2M tuples,
+// one level lower per factor of 8 above, the lowest from there on.
+int level_of(const dm_server* S, uint64_t tuples) {
+  int lvl = 0;
+  for (uint64_t v = tuples; v >= 2000000 && lvl < S->levels - 1; v /= 8) ++lvl;
+  return lvl;
+}
+
 // One scheduling round under the lock: collect finished slots, start
 // admissible requests.  Returns true when anything changed.
 bool round(dm_server* S) {
@@ -77,6 +93,7 @@ bool round(dm_server* S) {
     const dm::SchedRequest& r = S->sched->requests()[a.request];
     auto& t = S->tables.at(r.table);
     dm_ctx_use_region(sl.ctx, static_cast<char*>(S->pool) + a.offset, a.bytes);
+    sl.stream = sl.by_level[level_of(S, t.tuples)];
     dm_status st = dm_merge_table(sl.ctx, t.in.data(), (uint32_t)t.in.size(), t.out.data(), sl.stream, S->cfg.flags);
     if (st == DM_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = DM_ECUDA;
     if (st != DM_OK) {
@@ -124,11 +141,22 @@ dm_status dm_server_create(dm_server** out, int device, const dm_server_config* 
     delete S;
     return DM_ENOMEM;
   }
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+    cudaFree(S->pool);
+    delete S;
+    return DM_ECUDA;
+  }
+  S->greatest = greatest;
+  S->levels = std::min(dm_server::kLevels, least - greatest + 1);
   S->sched = new dm::Scheduler(cfg->scratch_budget, cfg->slots);
   S->slots.resize(cfg->slots);
   for (auto& sl : S->slots) {
-    if (dm_create(&sl.ctx, device, 0) != DM_OK ||
-        cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+    bool streams_ok = true;
+    for (int l = 0; l < S->levels && streams_ok; ++l)
+      streams_ok = cudaStreamCreateWithPriority(&sl.by_level[l], cudaStreamNonBlocking, S->greatest + l) == cudaSuccess;
+    sl.stream = sl.by_level[0];
+    if (!streams_ok || dm_create(&sl.ctx, device, 0) != DM_OK ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
       dm_server_destroy(S);
       return DM_ECUDA;
@@ -153,12 +181,14 @@ void dm_server_destroy(dm_server* S) {
   if (S->worker.joinable()) S->worker.join();
   cudaSetDevice(S->device);
   for (auto& sl : S->slots) {
-    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    for (cudaStream_t st : sl.by_level)
+      if (st) cudaStreamSynchronize(st);
     if (sl.ctx) {
       sl.ctx->arena = nullptr;   // the pool region is not the context's to free
       dm_destroy(sl.ctx);
     }
-    if (sl.stream) cudaStreamDestroy(sl.stream);
+    for (cudaStream_t st : sl.by_level)
+      if (st) cudaStreamDestroy(st);
     if (sl.done) cudaEventDestroy(sl.done);
   }
   if (S->pool) cudaFree(S->pool);

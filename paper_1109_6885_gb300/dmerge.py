@@ -30,6 +30,7 @@ DM_FLAG_X_GLOBAL = 0x4
 DM_FLAG_TIMING = 0x8
 DM_FLAG_SERIAL = 0x10
 DM_FLAG_AUTOTUNE = 0x20
+DM_FLAG_NO_GRAPH = 0x40
 DM_STAGE_AUTO, DM_STAGE_SMEM, DM_STAGE_GLOBAL = 0, 1, 2
 DM_X8_AUTO, DM_X8_OFF = 0, 1
 

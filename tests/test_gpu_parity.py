@@ -417,9 +417,10 @@ def _check_table(cols, results):
         assert np.array_equal(xm, ref.x_main) and np.array_equal(xd, ref.x_delta)
 
 
-@pytest.mark.parametrize("flags", [0, dm.DM_FLAG_SERIAL])
+@pytest.mark.parametrize("flags", [0, dm.DM_FLAG_SERIAL, dm.DM_FLAG_NO_GRAPH])
 def test_merge_table_parity(ctx, flags):
-    """Batched (one graph launch) and serial table merges vs the per-column oracle."""
+    """Batched (one graph launch, or the same schedule issued directly) and serial table
+    merges vs the per-column oracle."""
     import torch
     rng = np.random.default_rng(5)
     cols, dcols, results = _table(rng, 9, 300_007, 3_001, 300_000)
