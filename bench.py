@@ -570,7 +570,7 @@ def run_table(args):
             "ms_per_step": t_batched / args.steps, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "mixed u32/u64/u128", "data": "synthetic",
             "config": {"workload": args.workload, **TABLES[args.workload],
-                       "form": "one CUDA-graph launch per table (4 branches)",
+                       "form": "one CUDA-graph launch per table (8 branches)",
                        "launch_choices": "autotuned per column class" if tune else "library defaults",
                        "parallelism": f"the table's {len(specs)} columns shared over {world} GPU(s), longest first",
                        "l2": "inputs larger than L2"},

@@ -141,11 +141,14 @@ dm_status dm_merge_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_o
                           void* stream, uint32_t flags);
 
 /* Merge ncols columns of one table (Section 6.2.1 scheme (i): columns are
- * independent tasks).  Same contract as dm_merge_column per column; the
- * arena must hold dm_table_scratch_bytes (flags as passed here).
+ * independent tasks).  Same contract as dm_merge_column per column.  The
+ * arena must hold one column's scratch (DM_ENOMEM otherwise); the full
+ * batched schedule needs dm_table_scratch_bytes (flags as passed here), and
+ * with less the schedule runs on fewer branches.
  *
  * By default the table runs as ONE CUDA-graph launch: the columns' kernels
- * are recorded once, round-robin over four branches, so that the latency-
+ * are recorded once, round-robin over eight branches (dm_tuning.table_branches
+ * sets another count), so that the latency-
  * bound Step 1 of some columns overlaps the bandwidth-bound Step 2(b) of
  * others, and replayed on later calls with the same argument bytes (the
  * same buffers; up to eight argument sets are kept per context).  With
@@ -328,7 +331,10 @@ typedef struct {
   uint32_t reencode_obufs;   /* Step 2(b): output staging buffers per warp (1..2) */
   uint32_t host_chunks;      /* dm_merge_column_host: pieces the main vector is
                                 uploaded, re-encoded and downloaded in (1..32) */
-  uint32_t reserved[4];
+  uint32_t table_branches;   /* dm_merge_table: concurrent branches of the batched
+                                schedule (1..8; default 8), each with its own scratch
+                                region; fewer run when the arena holds fewer */
+  uint32_t reserved[3];
 } dm_tuning;
 
 dm_status dm_set_tuning(dm_ctx* ctx, const dm_tuning* tuning);

@@ -290,6 +290,13 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 }  // namespace
 
+size_t dm_table_scratch_bytes_for(const dm_column_in* in, uint32_t ncols, uint32_t flags, uint32_t branches) {
+  size_t mx = 0;
+  for (uint32_t c = 0; c < ncols; ++c) mx = std::max(mx, align_up(dm_scratch_bytes(&in[c], flags)));
+  if (flags & DM_FLAG_SERIAL) return mx;
+  return mx * std::max<uint32_t>(1, std::min(ncols, branches));
+}
+
 extern "C" {
 
 const char* dm_last_error(const dm_ctx* ctx) {
@@ -325,10 +332,7 @@ size_t dm_scratch_bytes(const dm_column_in* in, uint32_t) {
 }
 
 size_t dm_table_scratch_bytes(const dm_column_in* in, uint32_t ncols, uint32_t flags) {
-  size_t mx = 0;
-  for (uint32_t c = 0; c < ncols; ++c) mx = std::max(mx, align_up(dm_scratch_bytes(&in[c], flags)));
-  if (flags & DM_FLAG_SERIAL) return mx;
-  return mx * std::min<uint32_t>(ncols, dm_ctx::kTableStreams);
+  return dm_table_scratch_bytes_for(in, ncols, flags, dm_ctx::kTableBranches);
 }
 
 dm_status dm_create(dm_ctx** out, int device, size_t arena_bytes) {
@@ -583,7 +587,9 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
     dm_status st = check_column(&in[c], &out[c], true);
     if (st != DM_OK) return st;
   }
-  if (dm_table_scratch_bytes(in, ncols, flags) > ctx->arena_bytes) return DM_ENOMEM;
+  // one column's scratch at least; the batched schedule runs as many
+  // branches as the arena holds regions (up to the tuned or default count)
+  if (dm_table_scratch_bytes_for(in, ncols, flags | DM_FLAG_SERIAL, 1) > ctx->arena_bytes) return DM_ENOMEM;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
   cudaStream_t s = as_stream(stream);
   ctx->timing_valid = false;
@@ -614,11 +620,14 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
     return DM_OK;
   }
 
-  // batched: one CUDA graph holds every column's kernels on kTableStreams
-  // branches; it is recorded once per distinct argument set and replayed
-  const uint32_t S = std::min<uint32_t>(ncols, dm_ctx::kTableStreams);
+  // batched: one CUDA graph holds every column's kernels on a few branches
+  // (each with its own scratch region); it is recorded once per distinct
+  // argument set and replayed
   size_t region = 0;
   for (uint32_t c = 0; c < ncols; ++c) region = std::max(region, align_up(dm_scratch_bytes(&in[c], flags)));
+  uint32_t S = ctx->tuning.table_branches ? ctx->tuning.table_branches : dm_ctx::kTableBranches;
+  if (region && ctx->arena_bytes / region < S) S = (uint32_t)(ctx->arena_bytes / region);
+  S = std::max<uint32_t>(1, std::min<uint32_t>(S, ncols));
   if (flags & DM_FLAG_NO_GRAPH) {
     // the same schedule, issued on the branches' streams directly
     std::vector<dm::ReencodePlan> plans;
@@ -924,7 +933,7 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
 dm_status dm_set_tuning(dm_ctx* ctx, const dm_tuning* t) {
   if (!ctx || !t) return DM_EINVAL;
   if (t->reencode_warps > 16 || (t->reencode_stages && (t->reencode_stages < 2 || t->reencode_stages > 4)) ||
-      t->reencode_obufs > 2 || t->host_chunks > dm_ctx::kChunks)
+      t->reencode_obufs > 2 || t->host_chunks > dm_ctx::kChunks || t->table_branches > dm_ctx::kTableStreams)
     return DM_EINVAL;
   ctx->tuning = *t;
   return DM_OK;

@@ -35,7 +35,10 @@ struct dm_ctx {
   dm_tune_cache own_cache;                // launch choices per column class
   dm_tune_cache* tune_cache = &own_cache; // or a cache shared with other contexts
   // batched table merges: side streams, fork/join events, graph cache
-  static constexpr uint32_t kTableStreams = 4;
+  // branches of a batched table merge: kTableBranches by default (the
+  // arena dm_table_scratch_bytes asks for), at most kTableStreams, and no
+  // more than the arena holds scratch regions
+  static constexpr uint32_t kTableStreams = 8, kTableBranches = 8;
   cudaStream_t side[kTableStreams] = {};
   cudaEvent_t fork = nullptr;
   cudaEvent_t join[kTableStreams] = {};
@@ -57,3 +60,6 @@ struct dm_ctx {
 
 // Lend a region of device memory to a context as its arena (not owned).
 void dm_ctx_use_region(dm_ctx* ctx, void* ptr, size_t bytes);
+
+// dm_table_scratch_bytes for a batched schedule of `branches` branches.
+size_t dm_table_scratch_bytes_for(const dm_column_in* in, uint32_t ncols, uint32_t flags, uint32_t branches);

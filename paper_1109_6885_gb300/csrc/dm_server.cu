@@ -25,6 +25,10 @@
 #include "dm_internal.h"
 #include "dm_sched.h"
 
+// Branches of each slot's batched table merges: slots already run side by
+// side, so fewer than a table merged alone.
+constexpr uint32_t kSlotBranches = 4;
+
 struct dm_server {
   int device = 0;
   dm_server_config cfg{};
@@ -162,6 +166,7 @@ dm_status dm_server_create(dm_server** out, int device, const dm_server_config* 
       return DM_ECUDA;
     }
     sl.ctx->coop_share = cfg->slots;
+    sl.ctx->tuning.table_branches = kSlotBranches;
     dm_set_tune_cache(sl.ctx, &S->tune_cache);
   }
   S->worker = std::thread(worker_main, S);
@@ -205,7 +210,7 @@ dm_status dm_server_add_table(dm_server* S, uint32_t id, const dm_column_in* in,
   t.in.assign(in, in + ncols);
   t.out.assign(out, out + ncols);
   for (uint32_t c = 0; c < ncols; ++c) t.tuples += in[c].main_rows + in[c].delta_rows;
-  const uint64_t footprint = dm_table_scratch_bytes(in, ncols, S->cfg.flags);
+  const uint64_t footprint = dm_table_scratch_bytes_for(in, ncols, S->cfg.flags, kSlotBranches);
   if (!S->sched->add_table(id, footprint)) return DM_ENOMEM;
   S->tables.emplace(id, std::move(t));
   return DM_OK;

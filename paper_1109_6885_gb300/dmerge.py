@@ -79,7 +79,8 @@ class Tuning(ctypes.Structure):
         ("reencode_stages", ctypes.c_uint32),
         ("reencode_obufs", ctypes.c_uint32),
         ("host_chunks", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 4),
+        ("table_branches", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 3),
     ]
 
 
