@@ -189,24 +189,57 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def strip_comments(text: str) -> str:
+    """C/C++ source without its comments, whitespace runs collapsed to one
+    space (string and character literals kept as they are)."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        ch = text[i]
+        if ch in "\"'":
+            j = i + 1
+            while j < n and text[j] != ch:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(ch)
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def sources_digest(paths) -> str:
+    """sha256 over source files with their comments removed, so that a record
+    taken on a kernel stays valid across comment edits but not code edits."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in paths:
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(strip_comments(fh.read()).encode())
+        h.update(b"\0")
+    return h.hexdigest()
+
+
 def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
     committed ncu record under profiles/, or None when there is none or the
-    kernel's sources changed since it was taken."""
-    import hashlib
+    kernel's sources (comments aside) changed since it was taken."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.traffic.json")
     try:
         rec = json.load(open(path))[kernel]
     except (OSError, ValueError, KeyError):
         return None
-    h = hashlib.sha256()
     try:
-        for f in rec["sources"]:
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
+        digest = sources_digest(rec["sources"])
     except OSError:
         return None
-    if h.hexdigest() != rec.get("sources_sha256") or rec.get("workload") != workload:
+    if digest != rec.get("sources_sha256") or rec.get("workload") != workload:
         return None
     return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
 

@@ -425,7 +425,8 @@ dm_tune_cache* dm_get_tune_cache(dm_ctx* ctx);
 uint32_t dm_tune_candidates(const dm_ctx* ctx, const dm_column_in* in, dm_tune_choice* out, uint32_t cap);
 
 /* Merge the column (as dm_merge_column) under candidate choices, timing
- * `reps` merges of each (0: 5) with CUDA events on `stream`, and store the
+ * `reps` merges of each (0: 5; at most 1000, else DM_EINVAL) with CUDA
+ * events on `stream`, and store the
  * fastest in the context's tune cache.  The search takes the X_M staging
  * and byte-table choices first, then the Step 2(b) launch shape, then the
  * Step 1 grid, each time keeping the fastest so far.  On return `out` holds

@@ -409,7 +409,10 @@ class Context:
     @property
     def tune_cache(self) -> TuneCache:
         """The cache this context looks launch choices up in."""
-        return TuneCache(_load().dm_get_tune_cache(self.handle), owner=self)
+        h = _load().dm_get_tune_cache(self.handle)
+        if not h:
+            raise DmError(DM_EINVAL, "dm_get_tune_cache")
+        return TuneCache(h, owner=self)
 
     def set_tune_cache(self, cache: TuneCache | None):
         """Share `cache` (kept alive by this context); None: the context's own."""
@@ -678,7 +681,10 @@ class Server:
     @property
     def tune_cache(self) -> TuneCache:
         """The cache every slot looks its launch choices up in."""
-        return TuneCache(_load().dm_server_tune_cache(self.handle), owner=self)
+        h = _load().dm_server_tune_cache(self.handle)
+        if not h:
+            raise DmError(DM_EINVAL, "dm_server_tune_cache")
+        return TuneCache(h, owner=self)
 
 
 def dm_sched_simulate(pool_bytes: int, slots: int, footprint, service_ns, req_table, arrival_ns):
