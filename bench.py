@@ -90,6 +90,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--unopt", action="store_true",
+                   help="column workloads: also time Step 2(b) by binary search in U' (Section 5.2) against the "
+                        "translation tables")
     p.add_argument("--no-autotune", action="store_true",
                    help="table workloads: run on the library defaults instead of tuned launch choices")
     p.add_argument("--serve-slots", default=None,
@@ -410,6 +413,27 @@ def run_gpu(args):
 
     # roofline of the dominant kernel (Step 2(b) re-encode), bytes it must move
     reencode_ms = phase_ms[3] / max(calls, 1)
+
+    unopt = None
+    if args.unopt:
+        # Step 2(b) by the unoptimised route on the same merged column: the
+        # value of each tuple looked up in U' (Eq. 5) instead of X_M / X_D
+        nwords = dm.dm_packed_bytes(n_tuples, b_new) // 4
+        want = res.new_packed[:nwords].clone()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        dm.dm_reencode_search(ctx, cin, cout, stream)
+        for k in range(args.steps):
+            if flush is not None:
+                flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            dm.dm_reencode_search(ctx, cin, cout, stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ums = sorted(a.elapsed_time(b) for a, b in ev)[args.steps // 2]
+        unopt = {"ms_per_reencode": ums, "opt_reencode_ms": reencode_ms, "tables_speedup": ums / reencode_ms,
+                 "same_bytes": bool(torch.equal(want, res.new_packed[:nwords])),
+                 "status": ctx.sync_status()}
     step2 = traffic.step2_bytes(col.main_bits, b_new, col.n_main, col.n_delta, m, d)
     peak, peak_kind = measured_peaks()
     achieved = step2 / (reencode_ms / 1e3) / 1e9
@@ -458,6 +482,7 @@ def run_gpu(args):
                            "min": ps[0], "max": ps[-1]},
             "roofline": roofline,
             **({"warm": warm} if warm else {}),
+            **({"unopt": unopt} if unopt else {}),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -197,6 +197,16 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
                       const uint32_t* d_bits, uint32_t max_bits, uint32_t* out_packed,
                       void* stream, uint32_t flags);
 
+/* Step 2(b) by the paper's unoptimised route (Section 5.2, Eq. 5): each
+ * tuple's value is decoded through U_M (main rows) or D_dict (delta rows)
+ * and its new code found by binary search in U', with no translation
+ * tables.  `in` is the column; `out` holds a finished merge of it (new_dict,
+ * *d_new_dict_len and *d_new_bits as dm_merge_column left them); the packed
+ * vector out->new_packed is rewritten, byte for byte the same as the
+ * X_M / X_D route gives.  For measuring what the tables save and for
+ * cross-checking.  Asynchronous; data errors go to the status word. */
+dm_status dm_reencode_search(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* stream);
+
 /* ---- allocation-free variant ---- */
 
 /* Largest |U_M| + |U_D| that dm_merge_dicts_noalloc accepts. */

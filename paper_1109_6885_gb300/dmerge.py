@@ -47,7 +47,7 @@ EXPORTS = [
     "dm_tune_key_of", "dm_tune_cache_create", "dm_tune_cache_destroy", "dm_tune_cache_put",
     "dm_tune_cache_get", "dm_tune_cache_size", "dm_tune_cache_generation", "dm_tune_cache_clear",
     "dm_tune_cache_save", "dm_tune_cache_load", "dm_set_tune_cache", "dm_get_tune_cache",
-    "dm_tune_candidates", "dm_autotune_column",
+    "dm_tune_candidates", "dm_autotune_column", "dm_reencode_search",
 ]
 
 
@@ -238,6 +238,7 @@ def _load():
             "dm_get_tune_cache": ([vp], vp),
             "dm_tune_candidates": ([vp, pin, ctypes.POINTER(TuneChoice), u32], u32),
             "dm_autotune_column": ([vp, pin, pout, vp, u32, u32, ctypes.POINTER(TuneReport)], i32),
+            "dm_reencode_search": ([vp, pin, pout, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -456,6 +457,11 @@ def dm_autotune_column(ctx: Context, cin: ColumnIn, cout: ColumnOut, stream=None
                                       _stream(stream), flags, reps, ctypes.byref(rep)),
            "dm_autotune_column", ctx)
     return rep
+
+
+def dm_reencode_search(ctx: Context, cin: ColumnIn, cout: ColumnOut, stream=None):
+    _check(_load().dm_reencode_search(ctx.handle, ctypes.byref(cin), ctypes.byref(cout), _stream(stream)),
+           "dm_reencode_search", ctx)
 
 
 def dm_merge_table(ctx: Context, cins, couts, stream=None, flags: int = 0):
