@@ -72,6 +72,8 @@ def _load():
         lib.oracle_naive_reencode.argtypes = [u32, vp, u64, vp, u32, u64, vp, u64, vp, u64, vp, u64,
                                               u32, vp]
         lib.oracle_naive_reencode.restype = i32
+        lib.oracle_ingest_delta.argtypes = [u32, vp, u64, vp, vp, pu64]
+        lib.oracle_ingest_delta.restype = i32
         _lib = lib
         return lib
 
@@ -101,6 +103,19 @@ def packed_words(n: int, b: int) -> int:
 def new_width(u: int) -> int:
     """Step 2(a), Eq. 4."""
     return int(_load().oracle_new_width(u))
+
+
+def ingest_delta(w: int, values: np.ndarray):
+    """Delta ingest (Section 4): (D_dict in order of first arrival, one code per tuple)."""
+    v = _keys(values, w)
+    n = v.shape[0]
+    dd = _empty_keys(n, w)
+    codes = np.zeros(n, np.uint32)
+    d = ctypes.c_uint64(0)
+    rc = _load().oracle_ingest_delta(w, _p(v), n, _p(dd), _p(codes), ctypes.byref(d))
+    if rc:
+        raise OracleError(rc, "ingest_delta")
+    return dd[:d.value], codes
 
 
 def sort_delta(w: int, delta_dict: np.ndarray):

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <utility>
 #include <vector>
 
@@ -271,6 +272,32 @@ int oracle_naive_reencode(uint32_t w, const void* um, uint64_t m, const uint32_t
     if (c >= d || !find(load_key(ddict, c, w), &code)) return ORACLE_BAD_CODE;
     pack_code(out_words, n_main + r, b_new, code);
   }
+  return ORACLE_OK;
+}
+
+// Delta ingest (Section 4, Figure 5): values appended to the delta
+// partition in arrival order.  The partition's dictionary holds each
+// distinct value once; here it lists them in order of first arrival, and
+// each tuple's code is the position of its value in that list (the first
+// arrival of a value takes the next code, later arrivals reuse it).
+int oracle_ingest_delta(uint32_t w, const void* values, uint64_t n, void* dict_out, uint32_t* codes,
+                        uint64_t* d_out) {
+  if (!width_ok(w) || (n && (!values || !dict_out || !codes)) || !d_out) return ORACLE_BAD_ARG;
+  std::map<Key, uint32_t> seen;
+  uint64_t d = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const Key k = load_key(values, i, w);
+    auto it = seen.find(k);
+    if (it == seen.end()) {
+      seen.emplace(k, static_cast<uint32_t>(d));
+      store_key(dict_out, d, w, k);
+      codes[i] = static_cast<uint32_t>(d);
+      ++d;
+    } else {
+      codes[i] = it->second;
+    }
+  }
+  *d_out = d;
   return ORACLE_OK;
 }
 

@@ -278,3 +278,61 @@ def test_validation_errors():
     with pytest.raises(oracle.OracleError) as e:
         oracle.merge_column(8, um, synth.pack(np.array([0, 1, 0, 1], np.uint32), 1), 1, 4, dd, dc)
     assert e.value.code == oracle.BAD_ARG
+
+
+# ---------------------------------------------------------------- delta ingest (Section 4)
+
+def test_ingest_fig5_delta():
+    """Figure 5's delta: five tuples, 'charlie' at positions 1 and 3, four distinct values
+    (the Figure 6 prose), coded in order of first arrival."""
+    fx = json.load(open(os.path.join(GOLDEN, "fig5_fig6_example.json")))
+    vals = np.array([ascii_key(s) for s in fx["delta_tuples"]], np.uint64)
+    dd, codes = oracle.ingest_delta(8, vals)
+    assert dd.shape[0] == fx["printed"]["delta_dict_size"] == 4
+    p = fx["printed"]["charlie_delta_positions"]
+    assert codes[p[0]] == codes[p[1]]
+    assert list(codes) == [0, 1, 2, 1, 3]
+    assert [int(x) for x in dd] == [ascii_key(s) for s in ["zulu", "charlie", "bravo", "echo"]]
+
+
+def _ingest_brute(values):
+    """The definition restated: scan left to right, a value not seen before takes the next code."""
+    first, codes = [], []
+    for v in values:
+        if v not in first:
+            first.append(v)
+        codes.append(first.index(v))
+    return first, codes
+
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+@pytest.mark.parametrize("seed", range(6))
+def test_ingest_brute_force(w, seed):
+    rng = random.Random(seed * 31 + w)
+    n = rng.randint(0, 60)
+    pool = [rng.getrandbits(8 * w) for _ in range(rng.randint(1, 12))]
+    vals = [rng.choice(pool) for _ in range(n)]
+    if w == 16:
+        arr = np.array([[v >> 64, v & (2**64 - 1)] for v in vals], np.uint64).reshape(-1, 2)
+    else:
+        arr = np.array(vals, np.uint32 if w == 4 else np.uint64)
+    dd, codes = oracle.ingest_delta(w, arr)
+    first, want = _ingest_brute(vals)
+    got_dd = [(int(r[0]) << 64) | int(r[1]) for r in dd] if w == 16 else [int(x) for x in dd]
+    assert got_dd == first
+    assert [int(c) for c in codes] == want
+
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+def test_ingest_invariants(w):
+    """On a larger Zipf-shaped column: decoding gives the values back, the dictionary is
+    duplicate-free, and the first occurrences of the codes come in order 0, 1, 2, ..."""
+    col = synth.make_column(synth.ColumnSpec(n_main=10_000, m=5_000, w=w, n_delta=200_000, f_new=0.4,
+                                             dist="zipf", zipf_s=1.0, seed=synth.column_seed(21, w)))
+    vals = col.delta_dict[col.delta_codes]
+    dd, codes = oracle.ingest_delta(w, vals)
+    assert np.array_equal(dd[codes], vals)
+    assert np.unique(dd, axis=0).shape[0] == dd.shape[0]
+    _, first_pos = np.unique(codes, return_index=True)
+    assert np.all(np.diff(first_pos) > 0)
+    assert int(codes.max()) + 1 == dd.shape[0]
