@@ -90,6 +90,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--ingest", action="store_true",
+                   help="column workloads: also time delta ingest (Section 4) of the workload's delta rows")
     p.add_argument("--unopt", action="store_true",
                    help="column workloads: also time Step 2(b) by binary search in U' (Section 5.2) against the "
                         "translation tables")
@@ -414,6 +416,32 @@ def run_gpu(args):
     # roofline of the dominant kernel (Step 2(b) re-encode), bytes it must move
     reencode_ms = phase_ms[3] / max(calls, 1)
 
+    ingest = None
+    if args.ingest:
+        # delta ingest of the workload's delta rows in arrival order: the
+        # insertion-order dictionary and codes the merge reads
+        vals = dcol.delta_dict[dcol.delta_codes.long()]
+        nd = col.n_delta
+        igd = dm.key_tensor_empty(max(nd, 1), w)
+        igc = torch.empty(max(nd, 1), dtype=torch.int32, device=f"cuda:{local}")
+        igl = torch.zeros(1, dtype=torch.int64, device=f"cuda:{local}")
+        dm.dm_ingest_delta(ctx, w, vals, nd, igd, igc, igl, stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for k in range(args.steps):
+            if flush is not None:
+                flush.fill_(k & 0xFF)
+            ev[k][0].record(stream)
+            dm.dm_ingest_delta(ctx, w, vals, nd, igd, igc, igl, stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ims = sorted(a.elapsed_time(b) for a, b in ev)[args.steps // 2]
+        dl = int(igl.item())
+        same = dl == dcol.d and bool(torch.equal(igd[:dl], dcol.delta_dict)) and \
+            bool(torch.equal(igc[:nd], dcol.delta_codes))
+        ingest = {"rows": nd, "ms": ims, "rows_per_s": nd / (ims / 1e3), "dict": dl,
+                  "same_as_the_workload_delta": same, "status": ctx.sync_status()}
+
     unopt = None
     if args.unopt:
         # Step 2(b) by the unoptimised route on the same merged column: the
@@ -483,6 +511,7 @@ def run_gpu(args):
             "roofline": roofline,
             **({"warm": warm} if warm else {}),
             **({"unopt": unopt} if unopt else {}),
+            **({"ingest": ingest} if ingest else {}),
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

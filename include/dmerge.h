@@ -207,6 +207,19 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
  * cross-checking.  Asynchronous; data errors go to the status word. */
 dm_status dm_reencode_search(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* stream);
 
+/* ---- delta ingest ---- */
+
+/* Delta ingest (Section 4, Figure 5): n values appended to a column's delta
+ * partition, in arrival order (`values`, n keys of value_bytes each, device
+ * memory), become the delta form the merge reads: dict_out receives D_dict,
+ * each distinct value once in order of first arrival (capacity n keys), and
+ * codes_out[i] the position of value i in it; the device scalar
+ * *d_dict_len receives |D_dict|.  Scratch (dm_ingest_scratch_bytes) comes
+ * from the context's arena.  n is at most 2^30.  Asynchronous. */
+size_t dm_ingest_scratch_bytes(uint32_t value_bytes, uint64_t n);
+dm_status dm_ingest_delta(dm_ctx* ctx, uint32_t value_bytes, const void* values, uint64_t n, void* dict_out,
+                          uint32_t* codes_out, uint64_t* d_dict_len, void* stream);
+
 /* ---- allocation-free variant ---- */
 
 /* Largest |U_M| + |U_D| that dm_merge_dicts_noalloc accepts. */

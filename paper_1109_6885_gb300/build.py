@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdmerge.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["dm_api.cu", "dm_step1.cu", "dm_reencode.cu", "dm_server.cu", "dm_tune.cpp", "dm_unopt.cu"]
+SOURCES = ["dm_api.cu", "dm_step1.cu", "dm_reencode.cu", "dm_server.cu", "dm_tune.cpp", "dm_unopt.cu", "dm_ingest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", f"-I{INCLUDE}"]

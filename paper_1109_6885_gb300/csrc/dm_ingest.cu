@@ -1,0 +1,293 @@
+// Delta ingest (Section 4, Figure 5): tuples appended to a column's delta
+// partition in arrival order, turned into the delta form the merge reads:
+// D_dict, each distinct value once in order of first arrival, and one code
+// per tuple (the position of its value in D_dict).  The paper keeps the
+// distinct values in a CSB+ tree with the tuple ids of each value; the
+// insertion-order dictionary plus codes carries the same information.
+//
+// GPU form:
+//   1. a hash table of row indices: each slot holds the smallest row of one
+//      value (the row is the key's representative, so any width needs only
+//      32-bit atomics: claim an empty slot with a CAS, or lower the row of a
+//      slot whose representative equals the value with atomicMin);
+//      open addressing, linear probing, load at most one half;
+//   2. each row finds its slot; a row is a first arrival when the slot holds
+//      it; rows are cut into tiles of 1024 and each tile counts its first
+//      arrivals;
+//   3. one block scans the tile counts (the codes of each tile's first
+//      arrivals start at its scan value) and publishes |D_dict|;
+//   4. each tile numbers its first arrivals in row order, writes them to
+//      D_dict and the code to their slot;
+//   5. every row reads its code from its slot.
+// Every probe loop ends after at most the table's size; nothing waits.
+#include <stdint.h>
+
+#include "../../include/dmerge.h"
+#include "dm_common.cuh"
+#include "dm_ctx.h"
+
+namespace dm {
+
+namespace {
+
+constexpr uint32_t IG_THREADS = 256;
+constexpr uint32_t IG_PER_THREAD = 4;
+constexpr uint32_t IG_TILE = IG_THREADS * IG_PER_THREAD;   // rows per tile
+constexpr uint32_t IG_EMPTY = 0xFFFFFFFFu;
+constexpr uint64_t IG_MAX_ROWS = 1ull << 30;
+
+// Table slots for n rows: a power of two of at least 2n (and 64).
+uint64_t table_slots(uint64_t n) {
+  uint64_t c = 64;
+  while (c < 2 * n) c <<= 1;
+  return c;
+}
+
+// MurmurHash3's 32- and 64-bit finalisers (public domain mixing steps).
+__device__ __forceinline__ uint32_t mix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85ebca6bu;
+  h ^= h >> 13;
+  h *= 0xc2b2ae35u;
+  h ^= h >> 16;
+  return h;
+}
+__device__ __forceinline__ uint64_t mix64(uint64_t k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+__device__ __forceinline__ uint32_t hash_key(uint32_t v) { return mix32(v); }
+__device__ __forceinline__ uint32_t hash_key(uint64_t v) { return (uint32_t)mix64(v); }
+__device__ __forceinline__ uint32_t hash_key(const u128& v) { return (uint32_t)mix64(v.hi ^ mix64(v.lo)); }
+
+struct IngestArgs {
+  const void* values;
+  uint64_t n;
+  void* dict_out;
+  uint32_t* codes;
+  uint64_t* d_out;
+  uint32_t* table;       // [slots] smallest row of the slot's value, or IG_EMPTY
+  uint32_t* slot_code;   // [slots] code of the slot's value
+  uint32_t* slot_of;     // [n] each row's slot
+  uint32_t* tile_first;  // [tiles] first arrivals per tile, then their exclusive scan
+  uint64_t slots;
+  uint32_t tiles;
+  uint32_t* status;
+};
+
+// The slot of row r's value (after the table is complete), or slots if absent.
+template <class K>
+__device__ __forceinline__ uint64_t find_slot(const IngestArgs& a, const K* vals, const K& v) {
+  const uint64_t mask = a.slots - 1;
+  uint64_t s = hash_key(v) & mask;
+  for (uint64_t p = 0; p < a.slots; ++p, s = (s + 1) & mask) {
+    const uint32_t r = __ldg(a.table + s);
+    if (r == IG_EMPTY) return a.slots;
+    if (key_eq(load_key(vals + r), v)) return s;
+  }
+  return a.slots;
+}
+
+template <int W>
+__global__ void __launch_bounds__(IG_THREADS) ingest_insert_kernel(IngestArgs a) {
+  using K = typename KeyOf<W>::T;
+  const K* vals = static_cast<const K*>(a.values);
+  const uint64_t mask = a.slots - 1;
+  for (uint64_t r = (uint64_t)blockIdx.x * IG_THREADS + threadIdx.x; r < a.n; r += (uint64_t)gridDim.x * IG_THREADS) {
+    const K v = load_key(vals + r);
+    uint64_t s = hash_key(v) & mask;
+    bool placed = false;
+    for (uint64_t p = 0; p < a.slots && !placed; ++p, s = (s + 1) & mask) {
+      uint32_t cur = atomicCAS(a.table + s, IG_EMPTY, (uint32_t)r);
+      if (cur == IG_EMPTY) {
+        placed = true;   // claimed
+      } else if (key_eq(load_key(vals + cur), v)) {
+        atomicMin(a.table + s, (uint32_t)r);
+        placed = true;
+      }
+    }
+    if (!placed) flag_status(a.status, ST_TIMEOUT);   // cannot happen at load <= 1/2
+  }
+}
+
+// Rows' slots and each tile's count of first arrivals.
+template <int W>
+__global__ void __launch_bounds__(IG_THREADS) ingest_mark_kernel(IngestArgs a) {
+  using K = typename KeyOf<W>::T;
+  __shared__ uint32_t wsum[IG_THREADS / 32];
+  const K* vals = static_cast<const K*>(a.values);
+  for (uint32_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
+    uint32_t cnt = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < IG_PER_THREAD; ++q) {
+      const uint64_t r = (uint64_t)t * IG_TILE + threadIdx.x * IG_PER_THREAD + q;
+      if (r < a.n) {
+        const uint64_t s = find_slot(a, vals, load_key(vals + r));
+        if (s >= a.slots) {
+          flag_status(a.status, ST_TIMEOUT);
+          a.slot_of[r] = 0;
+          continue;
+        }
+        a.slot_of[r] = (uint32_t)s;
+        cnt += __ldg(a.table + s) == (uint32_t)r ? 1u : 0u;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (uint32_t w = 0; w < IG_THREADS / 32; ++w) tot += wsum[w];
+      a.tile_first[t] = tot;
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of the tile counts by one block; |D_dict| to *d_out.
+__global__ void __launch_bounds__(IG_THREADS) ingest_scan_kernel(IngestArgs a) {
+  __shared__ uint32_t wsum[IG_THREADS / 32];
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < a.tiles; base += IG_THREADS) {
+    const uint32_t t = base + threadIdx.x;
+    const uint32_t v = t < a.tiles ? a.tile_first[t] : 0u;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if ((threadIdx.x & 31) >= (uint32_t)o) inc += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    uint32_t before = 0, total = 0;
+    for (uint32_t w = 0; w < IG_THREADS / 32; ++w) {
+      if (w < (threadIdx.x >> 5)) before += wsum[w];
+      total += wsum[w];
+    }
+    const uint64_t c = carry;
+    if (t < a.tiles) a.tile_first[t] = (uint32_t)(c + before + inc - v);
+    __syncthreads();
+    if (threadIdx.x == 0) carry = c + total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.d_out = carry;
+}
+
+// First arrivals numbered in row order: D_dict and their slots' codes.
+template <int W>
+__global__ void __launch_bounds__(IG_THREADS) ingest_emit_kernel(IngestArgs a) {
+  using K = typename KeyOf<W>::T;
+  __shared__ uint32_t wsum[IG_THREADS / 32];
+  const K* vals = static_cast<const K*>(a.values);
+  K* dict = static_cast<K*>(a.dict_out);
+  for (uint32_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
+    uint32_t first[IG_PER_THREAD], cnt = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < IG_PER_THREAD; ++q) {
+      const uint64_t r = (uint64_t)t * IG_TILE + threadIdx.x * IG_PER_THREAD + q;
+      first[q] = r < a.n && __ldg(a.table + a.slot_of[r]) == (uint32_t)r ? 1u : 0u;
+      cnt += first[q];
+    }
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if ((threadIdx.x & 31) >= (uint32_t)o) inc += y;
+    }
+    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    uint32_t code = a.tile_first[t] + inc - cnt;
+    for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) code += wsum[w];
+#pragma unroll
+    for (uint32_t q = 0; q < IG_PER_THREAD; ++q) {
+      if (first[q]) {
+        const uint64_t r = (uint64_t)t * IG_TILE + threadIdx.x * IG_PER_THREAD + q;
+        if (code < a.n) {
+          dict[code] = load_key(vals + r);
+          a.slot_code[a.slot_of[r]] = code;
+        } else {
+          flag_status(a.status, ST_TIMEOUT);
+        }
+        ++code;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(IG_THREADS) ingest_codes_kernel(IngestArgs a) {
+  for (uint64_t r = (uint64_t)blockIdx.x * IG_THREADS + threadIdx.x; r < a.n; r += (uint64_t)gridDim.x * IG_THREADS)
+    a.codes[r] = __ldg(a.slot_code + a.slot_of[r]);
+}
+
+template <int W>
+cudaError_t launch_ingest(const IngestArgs& a, cudaStream_t s, uint32_t sm_count, uint64_t* launches) {
+  const uint64_t row_blocks = (a.n + IG_THREADS - 1) / IG_THREADS;
+  const uint32_t grid = (uint32_t)(row_blocks < (uint64_t)sm_count * 8 ? row_blocks : (uint64_t)sm_count * 8);
+  const uint32_t tgrid = a.tiles < sm_count * 8 ? a.tiles : sm_count * 8;
+  ingest_insert_kernel<W><<<grid, IG_THREADS, 0, s>>>(a);
+  ingest_mark_kernel<W><<<tgrid, IG_THREADS, 0, s>>>(a);
+  ingest_scan_kernel<<<1, IG_THREADS, 0, s>>>(a);
+  ingest_emit_kernel<W><<<tgrid, IG_THREADS, 0, s>>>(a);
+  ingest_codes_kernel<<<grid, IG_THREADS, 0, s>>>(a);
+  *launches += 5;
+  return cudaGetLastError();
+}
+
+size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+}  // namespace
+
+}  // namespace dm
+
+extern "C" size_t dm_ingest_scratch_bytes(uint32_t value_bytes, uint64_t n) {
+  (void)value_bytes;
+  const uint64_t slots = dm::table_slots(n);
+  const uint64_t tiles = (n + dm::IG_TILE - 1) / dm::IG_TILE;
+  return dm::round256(slots * 4) * 2 + dm::round256(n * 4) + dm::round256(tiles * 4 + 4);
+}
+
+extern "C" dm_status dm_ingest_delta(dm_ctx* ctx, uint32_t value_bytes, const void* values, uint64_t n,
+                                     void* dict_out, uint32_t* codes_out, uint64_t* d_dict_len, void* stream) {
+  const uint32_t w = value_bytes;
+  if (!ctx || (w != 4 && w != 8 && w != 16) || !d_dict_len || n > dm::IG_MAX_ROWS) return DM_EINVAL;
+  if (n && (!values || !dict_out || !codes_out)) return DM_EINVAL;
+  if (n && ((reinterpret_cast<uintptr_t>(values) | reinterpret_cast<uintptr_t>(dict_out)) & (w - 1))) return DM_EINVAL;
+  if (dm_ingest_scratch_bytes(w, n) > ctx->arena_bytes) return DM_ENOMEM;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n == 0) return cudaMemsetAsync(d_dict_len, 0, 8, s) == cudaSuccess ? DM_OK : DM_ECUDA;
+  dm::IngestArgs a{};
+  a.values = values;
+  a.n = n;
+  a.dict_out = dict_out;
+  a.codes = codes_out;
+  a.d_out = d_dict_len;
+  a.slots = dm::table_slots(n);
+  a.tiles = (uint32_t)((n + dm::IG_TILE - 1) / dm::IG_TILE);
+  char* p = static_cast<char*>(ctx->arena);
+  a.table = reinterpret_cast<uint32_t*>(p);
+  p += dm::round256(a.slots * 4);
+  a.slot_code = reinterpret_cast<uint32_t*>(p);
+  p += dm::round256(a.slots * 4);
+  a.slot_of = reinterpret_cast<uint32_t*>(p);
+  p += dm::round256(n * 4);
+  a.tile_first = reinterpret_cast<uint32_t*>(p);
+  a.status = ctx->status;
+  if (cudaMemsetAsync(a.table, 0xFF, a.slots * 4, s) != cudaSuccess) return DM_ECUDA;
+  cudaError_t e;
+  switch (w) {
+    case 4: e = dm::launch_ingest<4>(a, s, ctx->sm_count, &ctx->launches); break;
+    case 8: e = dm::launch_ingest<8>(a, s, ctx->sm_count, &ctx->launches); break;
+    default: e = dm::launch_ingest<16>(a, s, ctx->sm_count, &ctx->launches); break;
+  }
+  if (e != cudaSuccess) ctx->last_error = e;
+  return e == cudaSuccess ? DM_OK : DM_ECUDA;
+}

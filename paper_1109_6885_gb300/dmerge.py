@@ -47,7 +47,8 @@ EXPORTS = [
     "dm_tune_key_of", "dm_tune_cache_create", "dm_tune_cache_destroy", "dm_tune_cache_put",
     "dm_tune_cache_get", "dm_tune_cache_size", "dm_tune_cache_generation", "dm_tune_cache_clear",
     "dm_tune_cache_save", "dm_tune_cache_load", "dm_set_tune_cache", "dm_get_tune_cache",
-    "dm_tune_candidates", "dm_autotune_column", "dm_reencode_search",
+    "dm_tune_candidates", "dm_autotune_column", "dm_reencode_search", "dm_ingest_scratch_bytes",
+    "dm_ingest_delta",
 ]
 
 
@@ -239,6 +240,8 @@ def _load():
             "dm_tune_candidates": ([vp, pin, ctypes.POINTER(TuneChoice), u32], u32),
             "dm_autotune_column": ([vp, pin, pout, vp, u32, u32, ctypes.POINTER(TuneReport)], i32),
             "dm_reencode_search": ([vp, pin, pout, vp], i32),
+            "dm_ingest_scratch_bytes": ([u32, u64], sz),
+            "dm_ingest_delta": ([vp, u32, vp, u64, vp, vp, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -462,6 +465,19 @@ def dm_autotune_column(ctx: Context, cin: ColumnIn, cout: ColumnOut, stream=None
 def dm_reencode_search(ctx: Context, cin: ColumnIn, cout: ColumnOut, stream=None):
     _check(_load().dm_reencode_search(ctx.handle, ctypes.byref(cin), ctypes.byref(cout), _stream(stream)),
            "dm_reencode_search", ctx)
+
+
+def dm_ingest_scratch_bytes(w: int, n: int) -> int:
+    return int(_load().dm_ingest_scratch_bytes(w, n))
+
+
+def dm_ingest_delta(ctx: Context, w: int, values, n: int, dict_out, codes_out, d_len, stream=None):
+    """Appended values -> (D_dict in order of first arrival, codes); |D_dict| to the device scalar d_len."""
+    need = dm_ingest_scratch_bytes(w, n)
+    if need > ctx.arena_bytes:
+        ctx.reserve(need)
+    _check(_load().dm_ingest_delta(ctx.handle, w, _ptr(values), n, _ptr(dict_out), _ptr(codes_out), _ptr(d_len),
+                                   _stream(stream)), "dm_ingest_delta", ctx)
 
 
 def dm_merge_table(ctx: Context, cins, couts, stream=None, flags: int = 0):
