@@ -45,6 +45,10 @@ WORKLOADS = {
     # the same shape at 40% of the rows (for profiler captures: a few GB on the device)
     "column-40M-u64-zipf1-delta400k": dict(n_main=40_000_000, m=400_000, w=8, n_delta=400_000,
                                            f_new=0.3, dist="zipf", zipf_s=1.0),
+    # Figure 9's largest main partition: 1B rows of 8-byte values, 1% unique
+    # (10M values, 24 bits), delta 1% of main (host generation takes minutes)
+    "column-1B-u64-uniq1pct-delta1pct": dict(n_main=1_000_000_000, m=10_000_000, w=8, n_delta=10_000_000,
+                                             f_new=0.3, dist="uniform"),
     # 1M-row column over 100k uniform uint64 values at 17 bits, 10k-row delta, half new
     "column-1M-u64-delta10k": dict(n_main=1_000_000, m=100_000, w=8, n_delta=10_000, f_new=0.5,
                                    dist="uniform", pool=0),
