@@ -63,3 +63,17 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(dm, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         dm.load()
+
+
+def test_ingest_scratch_sizes(lib):
+    """Ingest scratch: two tables of a power of two of at least 2n slots (4 bytes each),
+    one slot index per row, one count per 1024-row tile (256-byte aligned pieces)."""
+    r = lambda v: (v + 255) // 256 * 256
+    for n in [0, 1, 31, 1024, 1025, 1_000_000, 123_456_789]:
+        slots = 64
+        while slots < 2 * n:
+            slots *= 2
+        tiles = (n + 1023) // 1024
+        want = 2 * r(slots * 4) + r(n * 4) + r(tiles * 4 + 4)
+        for w in (4, 8, 16):
+            assert dm.dm_ingest_scratch_bytes(w, n) == want
