@@ -253,6 +253,31 @@ def recorded_traffic(kernel: str, workload: str):
     return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
 
 
+def host_cpu():
+    """The host's CPU model and logical core count (the oracle uses one of them)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and v.strip():
+                model = v.strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model", "Hardware") and v.strip():
+                    model = v.strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "model": model or platform.machine()}
+
+
 def cpu_oracle_rate(col, budget_s: float = 20.0):
     """The oracle as it stands, one host core: tuples/s over whole-column merges."""
     import oracle
@@ -305,7 +330,7 @@ def run_reference(args):
         "dtype": f"u{8 * col.w}" if col.w < 16 else "u128", "data": "synthetic",
         "config": {"workload": args.workload, "sample": desc},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": desc},
+                         "sample": desc, "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -489,7 +514,8 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, reps, el = cpu_oracle_rate(col)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{reps} whole-column merge(s) of this workload, {el:.1f} s, one thread"}
+               "sample": f"{reps} whole-column merge(s) of this workload, {el:.1f} s, one thread",
+               "host": host_cpu()}
 
     if rank == 0:
         ps = sorted(per_step)

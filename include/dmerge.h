@@ -16,7 +16,10 @@
  * of Section 5.3 are outputs too.
  *
  * Steps, each a set of sm_103a kernels:
- *   1(a)  sort D_dict                 -> U_D, perm   (LSD radix sort)
+ *   1(a)  sort D_dict                 -> U_D, perm   (a radix partition on
+ *         the most significant varying byte, then a shared-memory sort of
+ *         each bucket; stable LSD radix passes when a bucket would exceed
+ *         2048 keys)
  *   1(b)  merge U_M with U_D, dedup   -> U', X_M, X_D (merge path + scan)
  *   2(a)  E'_C = ceil(log2 |U'|)      -> device scalar
  *   2(b)  re-encode M and D           -> new packed vector (Eq. 11)
@@ -71,7 +74,10 @@ typedef enum {
   DM_ECUDA = 5,      /* a CUDA runtime call failed */
   DM_ETIMEOUT = 6,   /* a bounded device-side wait gave up */
   DM_EBUSY = 7,      /* the request cannot be admitted now */
-  DM_ENOENT = 8      /* no such entry (tune cache lookup, missing file) */
+  DM_ENOENT = 8,     /* no such entry (tune cache lookup, missing file) */
+  DM_EINTERNAL = 9   /* an internal consistency check on the device failed (a
+                        write index out of range, a hash slot missing); the
+                        call's outputs are not valid.  Not caused by the data. */
 } dm_status;
 
 /* flags for dm_merge_column / dm_merge_table */
@@ -215,7 +221,9 @@ dm_status dm_reencode_search(dm_ctx* ctx, const dm_column_in* in, const dm_colum
  * each distinct value once in order of first arrival (capacity n keys), and
  * codes_out[i] the position of value i in it; the device scalar
  * *d_dict_len receives |D_dict|.  Scratch (dm_ingest_scratch_bytes) comes
- * from the context's arena.  n is at most 2^30.  Asynchronous. */
+ * from the context's arena.  n is at most 2^30.  Asynchronous.  No input is
+ * a data error; dm_sync_status reports DM_EINTERNAL if a row was left
+ * without a hash slot (impossible at the table's load of at most one half). */
 size_t dm_ingest_scratch_bytes(uint32_t value_bytes, uint64_t n);
 dm_status dm_ingest_delta(dm_ctx* ctx, uint32_t value_bytes, const void* values, uint64_t n, void* dict_out,
                           uint32_t* codes_out, uint64_t* d_dict_len, void* stream);
@@ -247,7 +255,9 @@ dm_status dm_ingest_delta(dm_ctx* ctx, uint32_t value_bytes, const void* values,
  * Arguments as dm_merge_dicts; m + d above DM_NOALLOC_MAX_ENTRIES returns
  * DM_EINVAL.  d_status, if not NULL, is a device word into which the kernel
  * ORs data errors (1: U_M not strictly increasing, 2: a bad insertion code,
- * 4: a wait timed out); the caller clears it.  Runs on the current device. */
+ * 4: a wait timed out, 16: an internal check failed); the caller clears it.  With d_status NULL nothing
+ * reports such errors: the outputs of a call on bad data (or one whose wait
+ * timed out) are then unchecked.  Runs on the current device. */
 dm_status dm_merge_dicts_noalloc(uint32_t value_bytes, const void* main_dict, uint64_t m,
                                  const void* ud, const uint32_t* perm, uint64_t d,
                                  void* new_dict, uint32_t* x_main, uint32_t* x_delta,
@@ -331,7 +341,8 @@ dm_status dm_sched_simulate(uint64_t pool_bytes, uint32_t slots, uint32_t ntable
 /* ---- status, timing, introspection ---- */
 
 /* Wait for `stream`, read and clear the context's device status word:
- * DM_OK, or the most severe of DM_ETIMEOUT, DM_EUNSORTED, DM_ECODE. */
+ * DM_OK, or the most severe of DM_ETIMEOUT, DM_EINTERNAL, DM_EUNSORTED,
+ * DM_ECODE, DM_EINVAL (a device width scalar above the call's bound). */
 dm_status dm_sync_status(dm_ctx* ctx, void* stream);
 
 /* Milliseconds of the last dm_merge_column issued with DM_FLAG_TIMING, from
@@ -457,6 +468,23 @@ uint32_t dm_tune_candidates(const dm_ctx* ctx, const dm_column_in* in, dm_tune_c
  * capture. */
 dm_status dm_autotune_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* out, void* stream,
                              uint32_t flags, uint32_t reps, dm_tune_report* report);
+
+/* ---- testing the bounded waits ----
+ *
+ * Every device-side wait of the merge (grid barriers, the look-back words
+ * of the sort passes and of the merge tiles) polls a bounded number of
+ * times, then ORs DM_ETIMEOUT's bit into the status word and lets the
+ * kernel run to its end, so a wait that cannot be satisfied never hangs the
+ * GPU.  This setting exercises that path: in Step 1 launches of this
+ * context, merge tile `withhold_tile` (merged positions [4096 t, 4096 t +
+ * 4096)) does not publish its look-back word, so the waits of the merge
+ * tiles after it run out, and every Step 1 wait gives up after
+ * `spin_limit` polls (0: the library's limit, about a second).  The merge
+ * then finishes with wrong codes and dm_sync_status returns DM_ETIMEOUT;
+ * every memory access stays in bounds.  DM_WAIT_TEST_OFF (with spin_limit
+ * 0) restores normal merges.  Not for production use. */
+#define DM_WAIT_TEST_OFF 0xFFFFFFFFu
+dm_status dm_set_wait_test(dm_ctx* ctx, uint32_t withhold_tile, uint32_t spin_limit);
 
 /* Kernels this context has launched so far. */
 uint64_t dm_launch_count(const dm_ctx* ctx);

@@ -257,6 +257,8 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
     a.dir_entries = plan.dir_entries;
     a.status = ctx->status;
     a.grid_cap = grid_cap;
+    a.spin_limit = ctx->test_spin_limit;
+    a.test_withhold = ctx->test_withhold;
     e = dm::launch_step1(w, a, s, ctx->sm_count, &ctx->launches);
     if (e != cudaSuccess) ctx->last_error = e;
   } else {
@@ -314,6 +316,7 @@ const char* dm_status_str(dm_status s) {
     case DM_ETIMEOUT: return "DM_ETIMEOUT";
     case DM_EBUSY: return "DM_EBUSY";
     case DM_ENOENT: return "DM_ENOENT";
+    case DM_EINTERNAL: return "DM_EINTERNAL";
   }
   return "DM_UNKNOWN";
 }
@@ -642,6 +645,8 @@ dm_status dm_merge_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, co
   put(&ctx->arena, sizeof(ctx->arena));
   put(&ctx->tuning, sizeof(ctx->tuning));
   put(&ctx->coop_share, sizeof(ctx->coop_share));
+  put(&ctx->test_spin_limit, sizeof(ctx->test_spin_limit));
+  put(&ctx->test_withhold, sizeof(ctx->test_withhold));
   const uint64_t tune_gen = dm_tune_cache_generation(ctx->tune_cache);
   put(&ctx->tune_cache, sizeof(ctx->tune_cache));
   put(&tune_gen, sizeof(tune_gen));
@@ -855,6 +860,7 @@ dm_status dm_sort_delta(dm_ctx* ctx, uint32_t w, const void* delta_dict, uint64_
   if (cudaMemsetAsync(cs.zero, 0, cs.zero_bytes, s) != cudaSuccess) return DM_ECUDA;
   cs.s1.phases = dm::S1_SORT;
   cs.s1.status = ctx->status;
+  cs.s1.spin_limit = ctx->test_spin_limit;
   if (dm::launch_step1(w, cs.s1, s, ctx->sm_count, &ctx->launches) != cudaSuccess) return DM_ECUDA;
   return cuda_status(dm::launch_sort_copy_out(w, cs.slots, d, ud_out, perm_out, s, &ctx->launches));
 }
@@ -889,6 +895,8 @@ dm_status dm_merge_dicts(dm_ctx* ctx, uint32_t w, const void* main_dict, uint64_
   a.d_bits = d_bits;
   a.phases = dm::S1_MERGE;
   a.status = ctx->status;
+  a.spin_limit = ctx->test_spin_limit;
+  a.test_withhold = ctx->test_withhold;
   return cuda_status(dm::launch_step1(w, a, s, ctx->sm_count, &ctx->launches));
 }
 
@@ -928,6 +936,13 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
   ra.tune_stages = ctx->tuning.reencode_stages;
   ra.tune_obufs = ctx->tuning.reencode_obufs;
   return cuda_status(dm::launch_reencode(main_bits, ra, as_stream(stream), ctx->sm_count, flags, &ctx->launches));
+}
+
+dm_status dm_set_wait_test(dm_ctx* ctx, uint32_t withhold_tile, uint32_t spin_limit) {
+  if (!ctx) return DM_EINVAL;
+  ctx->test_withhold = withhold_tile == DM_WAIT_TEST_OFF ? 0u : withhold_tile + 1;
+  ctx->test_spin_limit = spin_limit;
+  return DM_OK;
 }
 
 dm_status dm_set_tuning(dm_ctx* ctx, const dm_tuning* t) {
@@ -1066,6 +1081,7 @@ dm_status dm_sync_status(dm_ctx* ctx, void* stream) {
       return DM_ECUDA;
   }
   if (v & dm::ST_TIMEOUT) return DM_ETIMEOUT;
+  if (v & dm::ST_INTERNAL) return DM_EINTERNAL;
   if (v & dm::ST_UNSORTED) return DM_EUNSORTED;
   if (v & dm::ST_CODE) return DM_ECODE;
   if (v & dm::ST_WIDTH) return DM_EINVAL;

@@ -16,6 +16,8 @@ enum : uint32_t {
   ST_CODE = 2u,      // a code outside its dictionary (clamped)
   ST_TIMEOUT = 4u,   // a bounded wait gave up
   ST_WIDTH = 8u,     // device width scalar above the host bound
+  ST_INTERNAL = 16u, // an internal consistency check failed (a write index out
+                     // of range, a hash slot missing): the outputs are invalid
 };
 
 // Spin limit of every device-side wait (about a second with the backoff).

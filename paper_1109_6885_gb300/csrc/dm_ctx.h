@@ -55,6 +55,11 @@ struct dm_ctx {
   bool owns_arena = true;           // false: the arena is a region lent by a server
   uint32_t coop_share = 1;          // cooperative Step 1 grids get capacity / (branches * coop_share)
   uint64_t launches = 0;
+  // dm_set_wait_test: polls before a Step 1 wait gives up (0: the library's
+  // limit) and the merge tile (plus one; 0: none) that withholds its
+  // look-back word
+  uint32_t test_spin_limit = 0;
+  uint32_t test_withhold = 0;
 };
 
 

@@ -11,15 +11,19 @@
 //      32-bit atomics: claim an empty slot with a CAS, or lower the row of a
 //      slot whose representative equals the value with atomicMin);
 //      open addressing, linear probing, load at most one half;
-//   2. each row finds its slot; a row is a first arrival when the slot holds
-//      it; rows are cut into tiles of 1024 and each tile counts its first
-//      arrivals;
+//      a row's slot is final once it claims it or finds its value there,
+//      so the insert also records each row's slot;
+//   2. a row is a first arrival when its slot holds it; rows are cut into
+//      tiles of 1024 and each tile counts its first arrivals;
 //   3. one block scans the tile counts (the codes of each tile's first
 //      arrivals start at its scan value) and publishes |D_dict|;
 //   4. each tile numbers its first arrivals in row order, writes them to
 //      D_dict and the code to their slot;
 //   5. every row reads its code from its slot.
-// Every probe loop ends after at most the table's size; nothing waits.
+// Consecutive threads take consecutive rows, so the per-row loads and
+// stores are coalesced.  Every probe loop ends after at most the table's
+// size; nothing waits.  A row left without a slot (impossible at load at
+// most one half) is flagged as an internal error.
 #include <stdint.h>
 
 #include "../../include/dmerge.h"
@@ -79,19 +83,6 @@ struct IngestArgs {
   uint32_t* status;
 };
 
-// The slot of row r's value (after the table is complete), or slots if absent.
-template <class K>
-__device__ __forceinline__ uint64_t find_slot(const IngestArgs& a, const K* vals, const K& v) {
-  const uint64_t mask = a.slots - 1;
-  uint64_t s = hash_key(v) & mask;
-  for (uint64_t p = 0; p < a.slots; ++p, s = (s + 1) & mask) {
-    const uint32_t r = __ldg(a.table + s);
-    if (r == IG_EMPTY) return a.slots;
-    if (key_eq(load_key(vals + r), v)) return s;
-  }
-  return a.slots;
-}
-
 template <int W>
 __global__ void __launch_bounds__(IG_THREADS) ingest_insert_kernel(IngestArgs a) {
   using K = typename KeyOf<W>::T;
@@ -101,41 +92,46 @@ __global__ void __launch_bounds__(IG_THREADS) ingest_insert_kernel(IngestArgs a)
     const K v = load_key(vals + r);
     uint64_t s = hash_key(v) & mask;
     bool placed = false;
-    for (uint64_t p = 0; p < a.slots && !placed; ++p, s = (s + 1) & mask) {
+    for (uint64_t p = 0; p < a.slots; ++p, s = (s + 1) & mask) {
       uint32_t cur = atomicCAS(a.table + s, IG_EMPTY, (uint32_t)r);
       if (cur == IG_EMPTY) {
         placed = true;   // claimed
-      } else if (key_eq(load_key(vals + cur), v)) {
+        break;
+      }
+      if (key_eq(load_key(vals + cur), v)) {
         atomicMin(a.table + s, (uint32_t)r);
         placed = true;
+        break;
       }
     }
-    if (!placed) flag_status(a.status, ST_TIMEOUT);   // cannot happen at load <= 1/2
+    if (placed) {
+      a.slot_of[r] = (uint32_t)s;
+    } else {
+      flag_status(a.status, ST_INTERNAL);   // cannot happen at load <= 1/2
+      a.slot_of[r] = IG_EMPTY;
+    }
   }
 }
 
-// Rows' slots and each tile's count of first arrivals.
-template <int W>
+// Row q * IG_THREADS + threadIdx.x of tile t (consecutive threads, consecutive rows).
+__device__ __forceinline__ uint64_t tile_row(uint32_t t, uint32_t q) {
+  return (uint64_t)t * IG_TILE + (uint64_t)q * IG_THREADS + threadIdx.x;
+}
+
+// Whether row r is the first arrival of its value (its slot holds r).
+__device__ __forceinline__ bool first_arrival(const IngestArgs& a, uint64_t r) {
+  if (r >= a.n) return false;
+  const uint32_t s = a.slot_of[r];
+  return s != IG_EMPTY && __ldg(a.table + s) == (uint32_t)r;
+}
+
+// Each tile's count of first arrivals.
 __global__ void __launch_bounds__(IG_THREADS) ingest_mark_kernel(IngestArgs a) {
-  using K = typename KeyOf<W>::T;
   __shared__ uint32_t wsum[IG_THREADS / 32];
-  const K* vals = static_cast<const K*>(a.values);
   for (uint32_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
     uint32_t cnt = 0;
 #pragma unroll
-    for (uint32_t q = 0; q < IG_PER_THREAD; ++q) {
-      const uint64_t r = (uint64_t)t * IG_TILE + threadIdx.x * IG_PER_THREAD + q;
-      if (r < a.n) {
-        const uint64_t s = find_slot(a, vals, load_key(vals + r));
-        if (s >= a.slots) {
-          flag_status(a.status, ST_TIMEOUT);
-          a.slot_of[r] = 0;
-          continue;
-        }
-        a.slot_of[r] = (uint32_t)s;
-        cnt += __ldg(a.table + s) == (uint32_t)r ? 1u : 0u;
-      }
-    }
+    for (uint32_t q = 0; q < IG_PER_THREAD; ++q) cnt += first_arrival(a, tile_row(t, q)) ? 1u : 0u;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = cnt;
@@ -180,42 +176,39 @@ __global__ void __launch_bounds__(IG_THREADS) ingest_scan_kernel(IngestArgs a) {
   if (threadIdx.x == 0) *a.d_out = carry;
 }
 
-// First arrivals numbered in row order: D_dict and their slots' codes.
+// First arrivals numbered in row order: D_dict and their slots' codes.  A
+// tile's rows go in IG_PER_THREAD rounds of IG_THREADS consecutive rows; the
+// first arrivals before a row are those of earlier rounds, of earlier warps
+// in its round, and of lower lanes in its warp (one ballot each).
 template <int W>
 __global__ void __launch_bounds__(IG_THREADS) ingest_emit_kernel(IngestArgs a) {
   using K = typename KeyOf<W>::T;
-  __shared__ uint32_t wsum[IG_THREADS / 32];
+  constexpr uint32_t NW = IG_THREADS / 32;
+  __shared__ uint32_t wcnt[IG_PER_THREAD * NW];
   const K* vals = static_cast<const K*>(a.values);
   K* dict = static_cast<K*>(a.dict_out);
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t t = blockIdx.x; t < a.tiles; t += gridDim.x) {
-    uint32_t first[IG_PER_THREAD], cnt = 0;
+    uint32_t ball[IG_PER_THREAD];
 #pragma unroll
     for (uint32_t q = 0; q < IG_PER_THREAD; ++q) {
-      const uint64_t r = (uint64_t)t * IG_TILE + threadIdx.x * IG_PER_THREAD + q;
-      first[q] = r < a.n && __ldg(a.table + a.slot_of[r]) == (uint32_t)r ? 1u : 0u;
-      cnt += first[q];
+      ball[q] = __ballot_sync(0xFFFFFFFFu, first_arrival(a, tile_row(t, q)));
+      if (lane == 0) wcnt[q * NW + warp] = __popc(ball[q]);
     }
-    uint32_t inc = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-      if ((threadIdx.x & 31) >= (uint32_t)o) inc += y;
-    }
-    if ((threadIdx.x & 31) == 31) wsum[threadIdx.x >> 5] = inc;
     __syncthreads();
-    uint32_t code = a.tile_first[t] + inc - cnt;
-    for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) code += wsum[w];
+    uint32_t acc = a.tile_first[t], k = 0;
 #pragma unroll
     for (uint32_t q = 0; q < IG_PER_THREAD; ++q) {
-      if (first[q]) {
-        const uint64_t r = (uint64_t)t * IG_TILE + threadIdx.x * IG_PER_THREAD + q;
+      for (; k < q * NW + warp; ++k) acc += wcnt[k];
+      if ((ball[q] >> lane) & 1u) {
+        const uint32_t code = acc + __popc(ball[q] & lanemask_lt());
+        const uint64_t r = tile_row(t, q);
         if (code < a.n) {
           dict[code] = load_key(vals + r);
           a.slot_code[a.slot_of[r]] = code;
         } else {
-          flag_status(a.status, ST_TIMEOUT);
+          flag_status(a.status, ST_INTERNAL);
         }
-        ++code;
       }
     }
     __syncthreads();
@@ -223,8 +216,10 @@ __global__ void __launch_bounds__(IG_THREADS) ingest_emit_kernel(IngestArgs a) {
 }
 
 __global__ void __launch_bounds__(IG_THREADS) ingest_codes_kernel(IngestArgs a) {
-  for (uint64_t r = (uint64_t)blockIdx.x * IG_THREADS + threadIdx.x; r < a.n; r += (uint64_t)gridDim.x * IG_THREADS)
-    a.codes[r] = __ldg(a.slot_code + a.slot_of[r]);
+  for (uint64_t r = (uint64_t)blockIdx.x * IG_THREADS + threadIdx.x; r < a.n; r += (uint64_t)gridDim.x * IG_THREADS) {
+    const uint32_t s = a.slot_of[r];
+    a.codes[r] = s != IG_EMPTY ? __ldg(a.slot_code + s) : 0u;
+  }
 }
 
 template <int W>
@@ -233,7 +228,7 @@ cudaError_t launch_ingest(const IngestArgs& a, cudaStream_t s, uint32_t sm_count
   const uint32_t grid = (uint32_t)(row_blocks < (uint64_t)sm_count * 8 ? row_blocks : (uint64_t)sm_count * 8);
   const uint32_t tgrid = a.tiles < sm_count * 8 ? a.tiles : sm_count * 8;
   ingest_insert_kernel<W><<<grid, IG_THREADS, 0, s>>>(a);
-  ingest_mark_kernel<W><<<tgrid, IG_THREADS, 0, s>>>(a);
+  ingest_mark_kernel<<<tgrid, IG_THREADS, 0, s>>>(a);
   ingest_scan_kernel<<<1, IG_THREADS, 0, s>>>(a);
   ingest_emit_kernel<W><<<tgrid, IG_THREADS, 0, s>>>(a);
   ingest_codes_kernel<<<grid, IG_THREADS, 0, s>>>(a);

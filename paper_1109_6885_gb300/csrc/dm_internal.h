@@ -51,6 +51,12 @@ struct Step1Args {
   uint32_t* barriers;        // [S1_BARRIERS] (zeroed)
   uint32_t* status;
   uint32_t grid_cap;         // 0: whole device; else at most this many blocks
+  // bounded waits: polls of a look-back word or barrier before the wait
+  // gives up (0: kSpinLimit); testing: merge tile test_withhold - 1 never
+  // publishes its look-back word, so the waits of the tiles after it run
+  // out (0: none)
+  uint32_t spin_limit;
+  uint32_t test_withhold;
 };
 
 // Set the Step 1 kernels' launch attributes (outside any stream capture).

@@ -458,13 +458,17 @@ struct KernelTable<-1> {
   static void fill(KernelFn*) {}
 };
 
+// The raised shared-memory limit of a kernel holds for the device that was
+// current when it was set, so it is kept per device.
+constexpr int kRegDevices = 64;
 struct Registry {
   KernelFn fn[33];
-  uint32_t smem_set[33];  // dynamic smem size already allowed per kernel
+  uint32_t smem_set[kRegDevices][33];  // dynamic smem size already allowed per device and kernel
   std::mutex mu;
   Registry() {
     KernelTable<32>::fill(fn);
-    for (auto& s : smem_set) s = 0;
+    for (auto& d : smem_set)
+      for (auto& s : d) s = 0;
   }
 };
 
@@ -513,7 +517,7 @@ cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, 
   // (one block per SM); a lookup table that leaves room for fewer than 4
   // warps is dropped for the global gather
   int dev = 0, optin = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kRegDevices ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return cudaErrorInvalidValue;
   auto fit = [&](const Layout& l, uint32_t cap) {
@@ -536,10 +540,10 @@ cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, 
   P.fn = R.fn[b];
   {
     std::lock_guard<std::mutex> g(R.mu);
-    if (R.smem_set[b] < P.bytes) {
+    if (R.smem_set[dev][b] < P.bytes) {
       cudaError_t e = cudaFuncSetAttribute(P.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.bytes);
       if (e != cudaSuccess) return e;
-      R.smem_set[b] = P.bytes;
+      R.smem_set[dev][b] = P.bytes;
     }
   }
   int per_sm = 0;

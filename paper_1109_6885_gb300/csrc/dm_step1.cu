@@ -73,14 +73,18 @@ __device__ __forceinline__ K ld_key(const K* p, bool coherent) {
 // Barrier `idx` of this launch: every block adds one to its own zeroed
 // counter and waits (bounded) until all blocks have.  Writes before the
 // barrier are fenced; reads after it see them.
-__device__ void grid_barrier(uint32_t* bars, uint32_t idx, uint32_t* status) {
+__device__ __forceinline__ uint32_t spin_limit_of(const Step1Args& a) {
+  return a.spin_limit ? a.spin_limit : kSpinLimit;
+}
+
+__device__ void grid_barrier(uint32_t* bars, uint32_t idx, uint32_t* status, uint32_t limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     atomicAdd(&bars[idx], 1u);
     uint32_t spins = 0;
     while (ld_volatile(&bars[idx]) < gridDim.x) {
-      if (++spins > kSpinLimit) {
+      if (++spins > limit) {
         flag_status(status, ST_TIMEOUT);
         break;
       }
@@ -345,6 +349,7 @@ __device__ void pass_tile(const Step1Args& a, int pass, uint32_t tile, int e, co
     st_volatile(&lb[(uint64_t)tile * 256 + tid], LB_AGG32 | tcount);
     int64_t p = (int64_t)tile - 1;
     uint32_t spins = 0;
+    const uint32_t limit = spin_limit_of(a);
     bool done = false;
     while (!done && p >= 0) {
       uint32_t v[32];   // 32 predecessors per round trip
@@ -354,7 +359,7 @@ __device__ void pass_tile(const Step1Args& a, int pass, uint32_t tile, int e, co
       for (int q = 0; q < 32; ++q) {
         if (!done) {
           while ((v[q] >> 30) == 0) {   // not published yet
-            if (++spins > kSpinLimit) {
+            if (++spins > limit) {
               flag_status(a.status, ST_TIMEOUT);
               v[q] = LB_INC32;
               break;
@@ -395,7 +400,7 @@ __device__ void pass_tile(const Step1Args& a, int pass, uint32_t tile, int e, co
       dst_k[pos] = k;
       dst_v[pos] = S.vals[i];
     } else {
-      flag_status(a.status, ST_TIMEOUT);
+      flag_status(a.status, ST_INTERNAL);
     }
   }
   __syncthreads();
@@ -445,7 +450,7 @@ __device__ void msd_tile(const Step1Args& a, int top, uint32_t tile, const uint3
         dst_k[pos] = key[r];
         dst_v[pos] = (uint32_t)(tbase + (uint64_t)r * S1_THREADS);
       } else {
-        flag_status(a.status, ST_TIMEOUT);
+        flag_status(a.status, ST_INTERNAL);
       }
     }
   }
@@ -661,6 +666,20 @@ __device__ void bucket_sort_sub(const typename KeyOf<W>::T* src_k, const uint32_
   __syncthreads();
 }
 
+// Whether bucket [off, off + n) of the top-byte partition is one for the
+// shared-memory sort: more than one key, inside the d keys, at most BK_CAP.
+// The plan guarantees the last two unless a grid barrier before it timed out
+// (the histogram it read was then incomplete); such a bucket is skipped and
+// flagged, so that a timed-out wait never leads to an access out of bounds.
+__device__ __forceinline__ bool bucket_ok(const Step1Args& a, uint32_t off, uint32_t n) {
+  if (n <= 1) return false;
+  if (n > BK_CAP || (uint64_t)off + n > a.d) {
+    if (threadIdx.x == 0) flag_status(a.status, ST_INTERNAL);
+    return false;
+  }
+  return true;
+}
+
 // ---------------------------------------------------------------- Step 1(b)
 // Number of U_M entries among the first k merged positions (ties: U_M
 // first).  Whole warp; 32 probes per round narrow the range 33-fold.
@@ -698,7 +717,17 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   const uint64_t k0 = (uint64_t)tile * T;
   const uint64_t k1 = k0 + T < n ? k0 + T : n;
   if (precut) {
-    if (tid < 2) S.cut[tid] = __ldcg(a.cuts + tile + tid);
+    if (tid == 0) {
+      // co-ranks found by another kernel or phase; clamped to a consistent
+      // pair (c0 a co-rank of k0, c1 one of k1, both segments of
+      // non-negative length), which they are unless the wait that ordered
+      // them timed out: then the tile is wrong but stays in bounds
+      const uint64_t r0 = __ldcg(a.cuts + tile), r1 = __ldcg(a.cuts + tile + 1);
+      const uint64_t c0 = min(max(r0, k0 > d ? k0 - d : (uint64_t)0), min(k0, m));
+      const uint64_t lo1 = max(c0, k1 > d ? k1 - d : (uint64_t)0), hi1 = min(c0 + (k1 - k0), m);
+      S.cut[0] = c0;
+      S.cut[1] = min(max(r1, lo1), hi1);
+    }
   } else if (warp < 2) {
     const uint64_t c = corank_warp(A, m, B, d, warp == 0 ? k0 : k1, bcoh);
     if (lane == 0) S.cut[warp] = c;
@@ -838,18 +867,22 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
 
   // decoupled look-back: the whole block reads 256 predecessors per round
   // trip and sums them down to the nearest inclusive prefix
+  // (a tile the test setting names publishes nothing, so that the waits
+  // of the tiles after it run out)
+  const bool publish = a.test_withhold != tile + 1;
   if (tile == 0) {
     if (tid == 0) {
-      st_volatile(&a.merge_lb[0], LB_INC64 | ttotal);
+      if (publish) st_volatile(&a.merge_lb[0], LB_INC64 | ttotal);
       S.excl = 0;
     }
   } else {
     if (tid == 0) {
-      st_volatile(&a.merge_lb[tile], LB_AGG64 | ttotal);
+      if (publish) st_volatile(&a.merge_lb[tile], LB_AGG64 | ttotal);
       S.lb_sum = 0;
     }
     int64_t top = (int64_t)tile - 1;
     uint32_t spins = 0;
+    const uint32_t limit = spin_limit_of(a);
     for (;;) {
       const int64_t p = top - (int64_t)tid;
       const uint64_t v = p >= 0 ? ld_volatile(&a.merge_lb[p]) : LB_INC64;
@@ -860,7 +893,7 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
       const uint32_t nearest = S.nearest;
       const bool all_ready = __syncthreads_and(tid > nearest || (v >> 62) != 0);
       if (!all_ready) {
-        if (++spins > kSpinLimit) {
+        if (++spins > limit) {
           if (tid == 0) flag_status(a.status, ST_TIMEOUT);
           break;
         }
@@ -878,7 +911,7 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
     __syncthreads();
     if (tid == 0) {
       S.excl = S.lb_sum;
-      st_volatile(&a.merge_lb[tile], LB_INC64 | (S.lb_sum + ttotal));
+      if (publish) st_volatile(&a.merge_lb[tile], LB_INC64 | (S.lb_sum + ttotal));
     }
   }
   __syncthreads();
@@ -897,7 +930,7 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
       unew[code] = sA[x];
       a.xm[i0 + x] = (uint32_t)code;
     } else {
-      flag_status(a.status, ST_TIMEOUT);
+      flag_status(a.status, ST_INTERNAL);
     }
   }
   for (uint32_t j = tid; j < nb; j += S1_THREADS) {
@@ -905,7 +938,7 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
     const bool nondup = S.ndx[j + 1] != before;
     const uint64_t code = excl + S.rank[j] + before - (nondup ? 0u : 1u);
     if (code >= n) {
-      flag_status(a.status, ST_TIMEOUT);
+      flag_status(a.status, ST_INTERNAL);
       continue;
     }
     if (nondup) unew[code] = sB[j];
@@ -944,7 +977,7 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
       up = v0;
     } else {
       hist_phase<W>(a, U.hist);
-      grid_barrier(a.barriers, nbar++, a.status);
+      grid_barrier(a.barriers, nbar++, a.status, spin_limit_of(a));
       bool msd = false;
       const uint32_t run = plan_phase<W>(a, s_plan, s_wsum, &msd);
       if (msd) {
@@ -952,14 +985,14 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
         // buckets sorted in shared memory in place
         const int top = 31 - __clz(run);
         for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) msd_tile<W>(a, top, t, s_plan, U.sp.s);
-        grid_barrier(a.barriers, nbar++, a.status);
+        grid_barrier(a.barriers, nbar++, a.status, spin_limit_of(a));
         // the next byte below the top one that varies splits each bucket once more
         const uint32_t lower = run & ((1u << top) - 1u);
         const int sub = lower ? 31 - __clz(lower) : -1;
         for (uint32_t b = blockIdx.x; b < 256; b += gridDim.x) {
           const uint32_t off = s_plan[top * 256 + b];
           const uint32_t n = (b < 255 ? s_plan[top * 256 + b + 1] : (uint32_t)a.d) - off;
-          if (n <= 1) continue;
+          if (!bucket_ok(a, off, n)) continue;
           if (sub >= 0) bucket_sort_sub<W>(k0, v0, off, n, true, k0, v0, sub, U.bp.b);
           else bucket_sort<W>(k0, v0, off, n, true, k0, v0, U.bp.b);
         }
@@ -970,7 +1003,7 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
         for (int p = 0; p < W; ++p) {
           if (!((run >> p) & 1u)) continue;
           for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) pass_tile<W>(a, p, t, e, s_plan, U.sp.s);
-          grid_barrier(a.barriers, nbar++, a.status);
+          grid_barrier(a.barriers, nbar++, a.status, spin_limit_of(a));
           ++e;
         }
         const bool last_odd = (e - 1) & 1;
@@ -984,7 +1017,7 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
       a.final_slot[1] = const_cast<uint32_t*>(up);
     }
     // the merge reads what other blocks wrote
-    if (a.phases & (S1_MERGE | S1_DIR)) grid_barrier(a.barriers, nbar++, a.status);
+    if (a.phases & (S1_MERGE | S1_DIR)) grid_barrier(a.barriers, nbar++, a.status, spin_limit_of(a));
   }
   if ((a.phases & S1_MERGE) && a.m + a.d > 0) {
     // a merge of several waves of tiles finds every tile boundary first, one
@@ -1000,7 +1033,7 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
         const uint64_t c = corank_warp(static_cast<const K*>(a.a), a.m, ud, a.d, k, coherent);
         if (lane == 0) a.cuts[b] = c;
       }
-      grid_barrier(a.barriers, nbar++, a.status);
+      grid_barrier(a.barriers, nbar++, a.status, spin_limit_of(a));
     }
     // block b merges tile b; further tiles (a merge of several waves) are
     // taken in index order from a counter, so that a tile's look-back only
@@ -1015,7 +1048,7 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
     }
   }
   if ((a.phases & S1_DIR) && a.dir_entries > 0) {
-    grid_barrier(a.barriers, nbar++, a.status);
+    grid_barrier(a.barriers, nbar++, a.status, spin_limit_of(a));
     for (uint32_t b = blockIdx.x * S1_THREADS + threadIdx.x; b < a.dir_entries; b += gridDim.x * S1_THREADS)
       a.xdir[b] = xdir_entry<true>(a.xm, (uint32_t)a.m, a.dir_shift, b, a.x8 != nullptr);
     if (a.x8)
@@ -1098,7 +1131,7 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_bucket_kernel(Step1Args a
     for (uint32_t b = blockIdx.x; b < 256; b += gridDim.x) {
       const uint32_t off = U.sp.plan[top * 256 + b];
       const uint32_t n = (b < 255 ? U.sp.plan[top * 256 + b + 1] : (uint32_t)a.d) - off;
-      if (n <= 1) continue;
+      if (!bucket_ok(a, off, n)) continue;
       if (sub >= 0) bucket_sort_sub<W>(k0, v0, off, n, true, k0, v0, sub, U.bp.b);
       else bucket_sort<W>(k0, v0, off, n, true, k0, v0, U.bp.b);
     }
@@ -1179,48 +1212,59 @@ __global__ void sort_copy_kernel(void* const* slot, uint64_t d, typename KeyOf<W
   }
 }
 
+// Kernel attributes (the raised shared-memory limit) and occupancy hold for
+// the device that was current when they were set, so they are kept per
+// device.
+constexpr int kLaunchDevices = 64;
 struct Launch {
   std::mutex mu;
-  bool ready[3] = {false, false, false};
-  int per_sm[3] = {0, 0, 0};
+  bool ready[kLaunchDevices][3] = {};
+  int per_sm[kLaunchDevices][3] = {};
 };
 Launch& launch_state() {
   static Launch L;
   return L;
 }
 
+cudaError_t current_device(int* dev) {
+  cudaError_t e = cudaGetDevice(dev);
+  if (e != cudaSuccess) return e;
+  return *dev >= 0 && *dev < kLaunchDevices ? cudaSuccess : cudaErrorInvalidDevice;
+}
+
+// Blocks per SM of step1_kernel<W> on the current device (its attributes set
+// on first use there), or 0 with the error in *err.
 template <int W>
-cudaError_t prepare_w() {
+int prepare_w(cudaError_t* err) {
   const int wi = W == 4 ? 0 : (W == 8 ? 1 : 2);
+  int dev = 0;
+  *err = current_device(&dev);
+  if (*err != cudaSuccess) return 0;
   Launch& L = launch_state();
   std::lock_guard<std::mutex> g(L.mu);
-  if (L.ready[wi]) return cudaSuccess;
+  if (L.ready[dev][wi]) return L.per_sm[dev][wi];
   const size_t smem = step1_smem_bytes<W>();
   cudaError_t e = cudaFuncSetAttribute(step1_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (const void* fn : {(const void*)step1_merge_kernel<W>, (const void*)step1_hist_kernel<W>,
                          (const void*)step1_pass_kernel<W>, (const void*)step1_msd_kernel<W>,
                          (const void*)step1_bucket_kernel<W>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.per_sm[wi], step1_kernel<W>, S1_THREADS, smem);
-  if (e != cudaSuccess) return e;
-  L.ready[wi] = true;
-  return cudaSuccess;
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step1_kernel<W>, S1_THREADS, smem);
+  *err = e;
+  if (e != cudaSuccess) return 0;
+  L.per_sm[dev][wi] = per_sm;
+  L.ready[dev][wi] = true;
+  return per_sm;
 }
 
 
 template <int W>
 cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint64_t* launches) {
-  const int wi = W == 4 ? 0 : (W == 8 ? 1 : 2);
   const size_t smem = step1_smem_bytes<W>();
-  cudaError_t pe = prepare_w<W>();
+  cudaError_t pe = cudaSuccess;
+  const int per_sm = prepare_w<W>(&pe);
   if (pe != cudaSuccess) return pe;
-  Launch& L = launch_state();
-  int per_sm;
-  {
-    std::lock_guard<std::mutex> g(L.mu);
-    per_sm = L.per_sm[wi];
-  }
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const uint64_t full = (uint64_t)per_sm * sm_count;
   uint64_t cap = full;
@@ -1292,18 +1336,17 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
 }  // namespace
 
 cudaError_t step1_prepare() {
-  cudaError_t e = prepare_w<4>();
-  if (e == cudaSuccess) e = prepare_w<8>();
-  if (e == cudaSuccess) e = prepare_w<16>();
+  cudaError_t e = cudaSuccess;
+  prepare_w<4>(&e);
+  if (e == cudaSuccess) prepare_w<8>(&e);
+  if (e == cudaSuccess) prepare_w<16>(&e);
   return e;
 }
 
 uint32_t step1_capacity(uint32_t w, uint32_t sm_count) {
-  if (step1_prepare() != cudaSuccess) return 0;
-  Launch& L = launch_state();
-  std::lock_guard<std::mutex> g(L.mu);
-  const int wi = w == 4 ? 0 : (w == 8 ? 1 : 2);
-  return (uint32_t)L.per_sm[wi] * sm_count;
+  cudaError_t e = cudaSuccess;
+  const int per_sm = w == 4 ? prepare_w<4>(&e) : (w == 8 ? prepare_w<8>(&e) : prepare_w<16>(&e));
+  return e == cudaSuccess ? (uint32_t)per_sm * sm_count : 0u;
 }
 
 uint32_t sort_tiles(uint64_t d) { return (uint32_t)((d + RS_TILE - 1) / RS_TILE); }
@@ -1374,7 +1417,7 @@ extern "C" dm_status dm_merge_dicts_noalloc(uint32_t w, const void* main_dict, u
                                             uint32_t* x_delta, uint64_t* d_u, uint32_t* d_bits,
                                             uint32_t* d_status, void* stream) {
   if ((w != 4 && w != 8 && w != 16) || !d_u || !d_bits) return DM_EINVAL;
-  if (m + d > DM_NOALLOC_MAX_ENTRIES) return DM_EINVAL;
+  if (m > DM_NOALLOC_MAX_ENTRIES || d > DM_NOALLOC_MAX_ENTRIES - m) return DM_EINVAL;
   if ((m && (!main_dict || !x_main)) || (d && (!ud || !perm || !x_delta)) || (m + d && !new_dict)) return DM_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DM_ECUDA;

@@ -23,7 +23,7 @@ _lib = None
 _lock = threading.Lock()
 
 (DM_OK, DM_EINVAL, DM_ENOMEM, DM_EUNSORTED, DM_ECODE, DM_ECUDA, DM_ETIMEOUT, DM_EBUSY,
- DM_ENOENT) = range(9)
+ DM_ENOENT, DM_EINTERNAL) = range(10)
 DM_FLAG_GENERIC_REENCODE = 0x1
 DM_FLAG_X_SMEM = 0x2
 DM_FLAG_X_GLOBAL = 0x4
@@ -32,6 +32,7 @@ DM_FLAG_SERIAL = 0x10
 DM_FLAG_AUTOTUNE = 0x20
 DM_FLAG_NO_GRAPH = 0x40
 DM_STAGE_AUTO, DM_STAGE_SMEM, DM_STAGE_GLOBAL = 0, 1, 2
+DM_WAIT_TEST_OFF = 0xFFFFFFFF
 DM_X8_AUTO, DM_X8_OFF = 0, 1
 
 EXPORTS = [
@@ -48,7 +49,7 @@ EXPORTS = [
     "dm_tune_cache_get", "dm_tune_cache_size", "dm_tune_cache_generation", "dm_tune_cache_clear",
     "dm_tune_cache_save", "dm_tune_cache_load", "dm_set_tune_cache", "dm_get_tune_cache",
     "dm_tune_candidates", "dm_autotune_column", "dm_reencode_search", "dm_ingest_scratch_bytes",
-    "dm_ingest_delta",
+    "dm_ingest_delta", "dm_set_wait_test",
 ]
 
 
@@ -242,6 +243,7 @@ def _load():
             "dm_reencode_search": ([vp, pin, pout, vp], i32),
             "dm_ingest_scratch_bytes": ([u32, u64], sz),
             "dm_ingest_delta": ([vp, u32, vp, u64, vp, vp, vp, vp], i32),
+            "dm_set_wait_test": ([vp, u32, u32], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -432,6 +434,13 @@ class Context:
 
     def sync_status(self, stream=None) -> int:
         return int(_load().dm_sync_status(self.handle, _stream(stream)))
+
+    def set_wait_test(self, withhold_tile: int | None, spin_limit: int = 0):
+        """Testing the bounded waits: merge tile `withhold_tile` of later Step 1
+        launches withholds its look-back word and waits give up after
+        `spin_limit` polls; None (and 0) restores normal merges."""
+        t = DM_WAIT_TEST_OFF if withhold_tile is None else int(withhold_tile)
+        _check(_load().dm_set_wait_test(self.handle, t, int(spin_limit)), "dm_set_wait_test")
 
     def last_timing(self):
         """ms of Step 1(a), 1(b)+2(a), the X_M directory, the Step 2(b) kernel and the

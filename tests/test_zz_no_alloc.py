@@ -4,14 +4,18 @@ dm_merge_dicts_noalloc serves callers that cannot allocate device memory
 when they merge (their engine owns all of HBM through its own pools, or
 cudaMalloc's implicit synchronisation is not acceptable on their path); its
 scratch is a fixed array in the library's static device memory.  This test
-calls it through the C ABI twice in a row, a larger merge and then a smaller
-one (the second must not see the first call's leftovers), and compares every
-output with dm_merge_dicts on the same inputs; merges are exact integer work,
-so the comparison is bit-exact.  This file is collected last.
+calls it through the C ABI on merges in a row, the first at exactly the
+array's limit of DM_NOALLOC_MAX_ENTRIES entries (every merge tile of the
+array in use) and then smaller ones of every key width (each must not see
+the previous call's leftovers), and compares every output with
+dm_merge_dicts on the same inputs and with the oracle's Step 1(b); merges
+are exact integer work, so the comparisons are bit-exact.  This file is
+collected last.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from paper_1109_6885_gb300 import dmerge as dm
 
@@ -35,7 +39,10 @@ def test_noalloc_merge_matches_regular_entry_point():
     build.build()
     torch.cuda.set_device(0)
     ctx = dm.Context(0, 64 << 20)
-    for w, m, d, seed in [(8, 700_000, 300_000, 1), (16, 40_000, 9_000, 2)]:
+    limit = dm.DM_NOALLOC_MAX_ENTRIES
+    cases = [(8, limit - (1 << 20), 1 << 20, 3), (4, 700_000, 300_000, 1), (16, 40_000, 9_000, 2),
+             (8, 5_000, 1_234, 4)]
+    for w, m, d, seed in cases:
         um, dd = _inputs(w, m, d, seed)
         t_um, t_dd = dm.to_device(um), dm.to_device(dd)
         ud = dm.key_tensor_empty(d, w)
@@ -66,6 +73,14 @@ def test_noalloc_merge_matches_regular_entry_point():
         assert torch.equal(n0[:u], n1[:u])
         assert torch.equal(xm0, xm1)
         assert torch.equal(xd0, xd1)
+        # and both agree with the oracle's Step 1(b) on the oracle's own sort
+        r_ud, r_perm = oracle.sort_delta(w, dd)
+        r_new, r_xm, r_xd = oracle.merge_dicts(w, um, r_ud, r_perm)
+        assert u == r_new.shape[0]
+        assert int(sc1[1]) == oracle.new_width(u)
+        assert np.array_equal(dm.to_host(n1[:u], r_new.dtype).reshape(r_new.shape), r_new)
+        assert np.array_equal(xm1.numpy().view(np.uint32), r_xm)
+        assert np.array_equal(xd1.numpy().view(np.uint32), r_xd)
     ctx.close()
 
 
