@@ -108,6 +108,10 @@ def parse():
                    help="served workloads: dm_merge_table flags of the served arm (default: the workload's)")
     p.add_argument("--tune-cache", default=None,
                    help="table workloads: load tuned choices from this JSON file first, save them after")
+    p.add_argument("--verify", action="store_true",
+                   help="table and served workloads: after the timed regions, check with device checksums "
+                        "that every column's result is the same in every form (batched and plain; every served "
+                        "request and the same table merged alone)")
     return p.parse_args()
 
 
@@ -703,6 +707,17 @@ def run_table(args):
     clocks = sampler.stop()
     launches = (ctx.launches - launches0) // (args.steps + max(args.warmup, 3))
     t_serial, per_s, rate_s = timed(dm.DM_FLAG_SERIAL)
+    verify = None
+    if args.verify:
+        # the last merge of each form left its results in the outputs
+        dm.dm_merge_table(ctx, cins, couts, stream, 0)
+        batched = dm.column_digests(cins, couts, stream)
+        dm.dm_merge_table(ctx, cins, couts, stream, dm.DM_FLAG_SERIAL)
+        serial = dm.column_digests(cins, couts, stream)
+        torch.cuda.synchronize()
+        verify = {"columns": len(cins), "batched_equals_plain": batched == serial,
+                  "mismatched_columns": [j for j, (a, b) in enumerate(zip(batched, serial)) if a != b][:10],
+                  "status": ctx.sync_status(), "check": "dm_column_digest of U', E'_C and the packed codes"}
     if tune is not None:
         tune["speedup_vs_defaults"] = tune["defaults_ms_per_step"] / (t_batched / args.steps)
     step2 = 0
@@ -734,10 +749,91 @@ def run_table(args):
         }
         if tune is not None:
             line["autotune"] = tune
+        if verify is not None:
+            line["verify"] = verify
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def serve_specs(cfg, rank: int = 0):
+    """The served workload's tables: per table (ncols, distinct column specs),
+    drawn in a fixed order from one seeded generator (the same on every
+    call).  Column j of a table repeats distinct column j mod len(specs)."""
+    rng = np.random.default_rng(0x5E7E + rank)
+    out = []
+    for t in range(cfg["ntables"]):
+        ncols = int(rng.integers(cfg["cols"][0], cfg["cols"][1] + 1))
+        n_main = int(np.exp(rng.uniform(np.log(cfg["rows"][0]), np.log(cfg["rows"][1]))))
+        n_delta = max(1, int(n_main * np.exp(rng.uniform(np.log(0.001), np.log(0.1)))))
+        nsrc = min(ncols, cfg.get("distinct", ncols))
+        specs = []
+        for j in range(ncols):
+            m = int(np.exp(rng.uniform(np.log(2), np.log(n_main))))
+            spec = synth.ColumnSpec(n_main=n_main, m=m, w=int(rng.choice([4, 8, 16])), n_delta=n_delta,
+                                    f_new=float(rng.uniform(0, 0.5)), dist="zipf", zipf_s=0.8,
+                                    seed=synth.column_seed(5 + 1000 * rank + t, j))
+            if j < nsrc:
+                specs.append(spec)
+        out.append((ncols, specs))
+    return out
+
+
+def serve_tables(dm, cfg, rank: int = 0):
+    """The served workload's tables resident on the device: a list of
+    (cins, couts) per table (repeated columns share inputs and outputs), the
+    device buffers to keep alive as (DeviceColumn, DeviceResult) per distinct
+    column, and the specs.  Columns are generated on the host by a thread
+    pool (the generator is C code that releases the interpreter lock)."""
+    import concurrent.futures
+    specs = serve_specs(cfg, rank)
+    flat = [sp for _, sps in specs for sp in sps]
+    dev = []
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        for k in range(0, len(flat), 16):
+            for c in ex.map(synth.make_column, flat[k:k + 16]):
+                d = dm.DeviceColumn.from_numpy(c.w, c.main_dict, c.main_packed, c.main_bits, c.n_main,
+                                               c.delta_dict, c.delta_codes)
+                dev.append((d, dm.alloc_result(d, with_x=False)))
+                del c
+    tables, pos = [], 0
+    for ncols, sps in specs:
+        mine = dev[pos:pos + len(sps)]
+        pos += len(sps)
+        cins = [mine[j % len(sps)][0].cin() for j in range(ncols)]
+        couts = [mine[j % len(sps)][1].cout() for j in range(ncols)]
+        tables.append((cins, couts))
+    return tables, dev, specs
+
+
+def serve_verify(dm, tables, cfg, slots, flags, tabs, gaps, device):
+    """Every served request's result equals its table merged alone: the
+    server's per-request checksums (DM_SERVER_DIGEST) of each table merged
+    by itself, then of the same arrivals served together."""
+    srv = dm.Server(device, slots=slots, scratch_budget=cfg["budget"], flags=flags | dm.DM_SERVER_DIGEST)
+    for t, (cins, couts) in enumerate(tables):
+        srv.add_table(t, cins, couts)
+    solo = []
+    for t in range(len(tables)):
+        rid = srv.submit(t)
+        srv.drain()
+        solo.append(srv.info(rid).digest)
+    t0 = time.perf_counter()
+    due = t0
+    rids = []
+    for t, g in zip(tabs, gaps):
+        due += g
+        while time.perf_counter() < due:
+            time.sleep(0.0005)
+        rids.append((int(t), srv.submit(int(t))))
+    srv.drain()
+    bad = [(rid, t) for t, rid in rids if srv.info(rid).status != dm.DM_OK or srv.info(rid).digest != solo[t]]
+    st = srv.stats()
+    srv.close()
+    return {"requests": len(rids), "tables": len(tables), "mismatches": len(bad), "first_mismatches": bad[:5],
+            "peak_concurrency": st.peak_concurrency,
+            "check": "DM_SERVER_DIGEST per request against the table merged alone"}
 
 
 def run_serve(args):
@@ -754,32 +850,8 @@ def run_serve(args):
     build.build()
     dm.load()
     cfg = SERVES[args.workload]
-    rng = np.random.default_rng(0x5E7E + rank)
-    keep, tables = [], []
-    for t in range(cfg["ntables"]):
-        ncols = int(rng.integers(cfg["cols"][0], cfg["cols"][1] + 1))
-        n_main = int(np.exp(rng.uniform(np.log(cfg["rows"][0]), np.log(cfg["rows"][1]))))
-        n_delta = max(1, int(n_main * np.exp(rng.uniform(np.log(0.001), np.log(0.1)))))
-        nsrc = min(ncols, cfg.get("distinct", ncols))
-        cins, couts = [], []
-        for j in range(ncols):
-            m = int(np.exp(rng.uniform(np.log(2), np.log(n_main))))
-            spec = synth.ColumnSpec(n_main=n_main, m=m, w=int(rng.choice([4, 8, 16])), n_delta=n_delta,
-                                    f_new=float(rng.uniform(0, 0.5)), dist="zipf", zipf_s=0.8,
-                                    seed=synth.column_seed(5 + 1000 * rank + t, j))
-            if j < nsrc:
-                c = synth.make_column(spec)
-                d = dm.DeviceColumn.from_numpy(c.w, c.main_dict, c.main_packed, c.main_bits, c.n_main,
-                                               c.delta_dict, c.delta_codes)
-                r = dm.alloc_result(d, with_x=False)
-                keep.append((d, r))
-                cins.append(d.cin())
-                couts.append(r.cout())
-                del c
-            else:
-                cins.append(cins[j % nsrc])
-                couts.append(couts[j % nsrc])
-        tables.append((cins, couts))
+    tables, keep, _ = serve_tables(dm, cfg, rank)
+    rng = np.random.default_rng(0x5E7E + rank + 1)
     table_tuples = [int(sum(ci.main_rows + ci.delta_rows for ci in c)) for c, _ in tables]
     nreq = max(args.steps * 10, cfg["requests"])
     tabs = rng.integers(0, cfg["ntables"], nreq)
@@ -838,6 +910,7 @@ def run_serve(args):
         sweep.append({"slots": k, "value": r["value"], "latency_ms": r["latency_ms"], "failed": r["failed"],
                       "peak_concurrency": r["peak_concurrency"]})
     plain = arm(1, dm.DM_FLAG_SERIAL, False)
+    verify = serve_verify(dm, tables, cfg, slot_counts[0], served_flags, tabs, gaps, local) if args.verify else None
     if rank == 0:
         line = {
             "metric": "served merged tuple-columns/s; p50/p99 merge latency", "value": served["value"],
@@ -856,6 +929,7 @@ def run_serve(args):
                       "value": plain["value"], "latency_ms": plain["latency_ms"], "failed": plain["failed"],
                       "slowest": plain["slowest"]},
             **({"slots_sweep": sweep} if sweep else {}),
+            **({"verify": verify} if verify else {}),
         }
         print(json.dumps(line), flush=True)
 

@@ -264,6 +264,21 @@ dm_status dm_merge_dicts_noalloc(uint32_t value_bytes, const void* main_dict, ui
                                  uint64_t* d_u, uint32_t* d_bits, uint32_t* d_status,
                                  void* stream);
 
+/* ---- result checksum ---- */
+
+/* Add a 64-bit checksum of one merged column's outputs to the device word
+ * *d_digest (zero it first; modulo 2^64): |U'| and E'_C as the device scalars
+ * hold them, the |U'| keys of new_dict and the dm_packed_bytes(N_M + N_D,
+ * E'_C) bytes of new_packed (X_M and X_D are not included).  Each 32-bit
+ * word adds splitmix64's output function of its position (col_index, which
+ * part, word index) and value, so equal results give equal sums in any
+ * order and a changed word changes the sum unless two terms cancel.  For
+ * comparing results of merges run in different forms (batched, plain,
+ * served) without copying them.  `in` and `out` as given to the merge;
+ * asynchronous on `stream`.  The paper has no counterpart. */
+dm_status dm_column_digest(const dm_column_in* in, const dm_column_out* out, uint32_t col_index,
+                           uint64_t* d_digest, void* stream);
+
 /* ---- served merges (continuous batching) ---- */
 
 /* A merge server: registered tables stay resident on the device; merge
@@ -284,8 +299,16 @@ typedef struct dm_server dm_server;
 typedef struct {
   uint32_t slots;            /* concurrent table merges, 1..16 */
   uint64_t scratch_budget;   /* bytes of the scratch pool: the admission budget */
-  uint32_t flags;            /* passed to dm_merge_table (0: one graph launch per table) */
+  uint32_t flags;            /* passed to dm_merge_table (0: one graph launch per table),
+                                plus the server's own DM_SERVER_* bits */
 } dm_server_config;
+
+/* dm_server_config.flags: after each merge, a kernel on the merge's stream
+ * sums a 64-bit checksum of its outputs (every column's |U'|, E'_C, U' and
+ * packed vector; X_M and X_D are not included) into the request's
+ * dm_request_info.digest, so that a merge served among others can be
+ * compared with the same merge run alone.  Costs one read of the outputs. */
+#define DM_SERVER_DIGEST 0x1000u
 
 typedef struct {
   uint32_t table_id;
@@ -293,6 +316,10 @@ typedef struct {
   uint64_t submit_ns, admit_ns, done_ns;   /* server clock (steady, from creation) */
   uint64_t footprint;        /* scratch bytes it held */
   uint32_t slot;
+  uint32_t automatic;        /* 1: requested by an online table's trigger */
+  uint64_t version;          /* version of the table the merge committed (0: none) */
+  uint64_t delta_rows;       /* online tables: delta rows the merge took */
+  uint64_t digest;           /* DM_SERVER_DIGEST: checksum of the outputs (0 otherwise) */
 } dm_request_info;
 
 typedef struct {
@@ -326,6 +353,113 @@ dm_status dm_server_request_info(dm_server* server, uint64_t request_id, dm_requ
 dm_status dm_server_stats_get(dm_server* server, dm_server_stats* stats);
 /* Committed merges of the table so far. */
 uint64_t dm_server_table_version(dm_server* server, uint32_t table_id);
+
+/* ---- online tables (the merge while inserts go on, Sections 3 and 4) ----
+ *
+ * An online table is owned by the server: its main partition (per column
+ * the sorted dictionary U_M and the packed codes) lives in server memory in
+ * two copies, and it has two delta partitions, each holding the raw values
+ * of inserted rows in arrival order (the paper's uncompressed delta).
+ * Inserts append to the active delta.  When a merge of the table is
+ * admitted, the active delta is frozen and the other, empty delta becomes
+ * active: rows inserted while the merge runs collect there (the paper's
+ * temporary second delta).  The merge combines the committed main with the
+ * frozen delta (D_dict = the frozen rows' values, row r coded r: repeated
+ * values are tolerated, Eq. 3) into the other main copy; its commit at
+ * completion makes that copy the table's main (version + 1) and empties the
+ * frozen delta, so the second delta is what the next merge takes.  With a
+ * trigger fraction k > 0, a merge is requested automatically as soon as the
+ * active delta holds more than k * N_M rows (Section 4: merge when N_D
+ * exceeds a fraction of N_M).  A paused table's merges are not admitted
+ * (inserts and the trigger go on); resuming lets them start.  A merge that
+ * has started runs to its end.  A merge that fails keeps its frozen delta,
+ * and the table's next merge takes that delta again. */
+typedef struct {
+  uint32_t value_bytes;      /* 4, 8 or 16 */
+  const void* main_dict;     /* initial U_M (device memory, copied at registration) */
+  uint64_t main_dict_len;    /* its length */
+  const void* main_packed;   /* initial packed codes (device memory, copied) */
+  uint32_t main_bits;        /* their width, >= dm_bits_for(main_dict_len) */
+} dm_online_column;
+
+typedef struct {
+  uint64_t main_rows;        /* N_M of the initial main */
+  uint64_t rows_capacity;    /* most rows the main may reach (>= main_rows) */
+  uint64_t delta_capacity;   /* most rows one delta holds */
+  double trigger;            /* k of the merge trigger N_D > k N_M; 0: merges only on request */
+} dm_online_config;
+
+/* Register online table `table_id` with ncols columns.  The server
+ * allocates its two main copies (per column main_dict_len + rows_capacity -
+ * main_rows keys and dm_packed_bytes(rows_capacity, bits of that) bytes
+ * each), its two deltas (delta_capacity keys per column each) and its
+ * scratch footprint at those capacities.  DM_ENOMEM: device memory or the
+ * pool is too small for it. */
+dm_status dm_server_add_online_table(dm_server* server, uint32_t table_id, uint32_t ncols,
+                                     const dm_online_column* cols, const dm_online_config* cfg);
+
+/* Where dm_server_insert put the rows. */
+typedef struct {
+  uint32_t delta;            /* delta partition (0 or 1) they were appended to */
+  uint64_t first_row;        /* their first row in it */
+  uint64_t lands_in;         /* the table version that will contain them */
+  uint32_t triggered;        /* 1: the insert requested a merge (request id below) */
+  uint64_t request;
+} dm_insert_info;
+
+/* Append nrows rows to an online table: values[c] holds the rows' nrows
+ * values of column c (value_bytes each; device or host memory).  Returns
+ * once the rows are copied into the active delta (the caller's buffers are
+ * free again).  DM_EBUSY: the active delta, or the main's row capacity,
+ * cannot take them (nothing is appended); retry after the next commit.
+ * info may be NULL. */
+dm_status dm_server_insert(dm_server* server, uint32_t table_id, uint64_t nrows, const void* const* values,
+                           dm_insert_info* info);
+
+/* Pause (paused != 0) or resume the merges of a table. */
+dm_status dm_server_pause(dm_server* server, uint32_t table_id, int paused);
+
+/* The committed state of column `col` of an online table. */
+typedef struct {
+  uint64_t version;          /* committed merges */
+  const void* main_dict;     /* U_M of that version (device memory, server-owned) */
+  uint64_t main_dict_len;
+  const void* main_packed;   /* its packed codes */
+  uint32_t main_bits;
+  uint64_t main_rows;
+  uint64_t delta_rows;       /* rows inserted and not in this version yet */
+} dm_online_view;
+
+/* The buffers stay as they are until the merge that produces version +2
+ * is admitted (merges alternate between the two main copies). */
+dm_status dm_server_online_view(dm_server* server, uint32_t table_id, uint32_t col, dm_online_view* view);
+
+/* Copy the committed version of column `col` out (host or device memory):
+ * its main_dict_len keys to dict_dst (dict_bytes at least that many bytes)
+ * and its dm_packed_bytes(main_rows, main_bits) bytes of codes to
+ * packed_dst, taken while no commit can swap the version; *view describes
+ * what was copied.  Synchronous.  DM_EINVAL: a buffer too small. */
+dm_status dm_server_online_copy(dm_server* server, uint32_t table_id, uint32_t col, void* dict_dst,
+                                size_t dict_bytes, void* packed_dst, size_t packed_bytes, dm_online_view* view);
+
+/* The online rules on a fake clock (no GPU), for testing and planning:
+ * ntables online tables (main_rows[t], delta_capacity[t], trigger[t]; rows
+ * capacity unbounded), each merge of table t taking service_ns[t], `slots`
+ * merges at once.  Events in time order (ev_ns non-decreasing): kind 0
+ * inserts ev_rows rows, 1 requests a merge, 2 pauses the table, 3 resumes
+ * it.  For every insert, ev_lands_in receives the version the insert said
+ * its rows would land in and ev_version the version whose merge actually
+ * took them (0 if rejected or never merged).  Merges, in admission order,
+ * go to merge_table / merge_admit_ns / merge_done_ns / merge_rows /
+ * merge_version / merge_automatic (at most max_merges; *nmerges receives
+ * how many ran). */
+dm_status dm_online_simulate(uint32_t slots, uint32_t ntables, const uint64_t* main_rows,
+                             const uint64_t* delta_capacity, const double* trigger, const uint64_t* service_ns,
+                             uint64_t nevents, const uint32_t* ev_kind, const uint32_t* ev_table,
+                             const uint64_t* ev_rows, const uint64_t* ev_ns, uint64_t* ev_lands_in,
+                             uint64_t* ev_version, uint64_t max_merges, uint32_t* merge_table,
+                             uint64_t* merge_admit_ns, uint64_t* merge_done_ns, uint64_t* merge_rows,
+                             uint64_t* merge_version, uint32_t* merge_automatic, uint64_t* nmerges);
 
 /* The server's admission rules run on a fake clock (no GPU): requests of
  * table req_table[i] arrive at arrival_ns[i] (non-decreasing); a merge of

@@ -33,6 +33,7 @@ DM_FLAG_AUTOTUNE = 0x20
 DM_FLAG_NO_GRAPH = 0x40
 DM_STAGE_AUTO, DM_STAGE_SMEM, DM_STAGE_GLOBAL = 0, 1, 2
 DM_WAIT_TEST_OFF = 0xFFFFFFFF
+DM_SERVER_DIGEST = 0x1000
 DM_X8_AUTO, DM_X8_OFF = 0, 1
 
 EXPORTS = [
@@ -49,7 +50,9 @@ EXPORTS = [
     "dm_tune_cache_get", "dm_tune_cache_size", "dm_tune_cache_generation", "dm_tune_cache_clear",
     "dm_tune_cache_save", "dm_tune_cache_load", "dm_set_tune_cache", "dm_get_tune_cache",
     "dm_tune_candidates", "dm_autotune_column", "dm_reencode_search", "dm_ingest_scratch_bytes",
-    "dm_ingest_delta", "dm_set_wait_test",
+    "dm_ingest_delta", "dm_set_wait_test", "dm_server_add_online_table", "dm_server_insert",
+    "dm_server_pause", "dm_server_online_view", "dm_online_simulate", "dm_server_online_copy",
+    "dm_column_digest",
 ]
 
 
@@ -137,7 +140,33 @@ class RequestInfo(ctypes.Structure):
     _fields_ = [("table_id", ctypes.c_uint32), ("status", ctypes.c_int32),
                 ("submit_ns", ctypes.c_uint64), ("admit_ns", ctypes.c_uint64),
                 ("done_ns", ctypes.c_uint64), ("footprint", ctypes.c_uint64),
-                ("slot", ctypes.c_uint32)]
+                ("slot", ctypes.c_uint32), ("automatic", ctypes.c_uint32),
+                ("version", ctypes.c_uint64), ("delta_rows", ctypes.c_uint64),
+                ("digest", ctypes.c_uint64)]
+
+
+class OnlineColumn(ctypes.Structure):
+    _fields_ = [("value_bytes", ctypes.c_uint32), ("main_dict", ctypes.c_void_p),
+                ("main_dict_len", ctypes.c_uint64), ("main_packed", ctypes.c_void_p),
+                ("main_bits", ctypes.c_uint32)]
+
+
+class OnlineConfig(ctypes.Structure):
+    _fields_ = [("main_rows", ctypes.c_uint64), ("rows_capacity", ctypes.c_uint64),
+                ("delta_capacity", ctypes.c_uint64), ("trigger", ctypes.c_double)]
+
+
+class InsertInfo(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_uint32), ("first_row", ctypes.c_uint64),
+                ("lands_in", ctypes.c_uint64), ("triggered", ctypes.c_uint32),
+                ("request", ctypes.c_uint64)]
+
+
+class OnlineView(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_uint64), ("main_dict", ctypes.c_void_p),
+                ("main_dict_len", ctypes.c_uint64), ("main_packed", ctypes.c_void_p),
+                ("main_bits", ctypes.c_uint32), ("main_rows", ctypes.c_uint64),
+                ("delta_rows", ctypes.c_uint64)]
 
 
 class ServerStats(ctypes.Structure):
@@ -244,6 +273,15 @@ def _load():
             "dm_ingest_scratch_bytes": ([u32, u64], sz),
             "dm_ingest_delta": ([vp, u32, vp, u64, vp, vp, vp, vp], i32),
             "dm_set_wait_test": ([vp, u32, u32], i32),
+            "dm_server_add_online_table": ([vp, u32, u32, ctypes.POINTER(OnlineColumn),
+                                            ctypes.POINTER(OnlineConfig)], i32),
+            "dm_server_insert": ([vp, u32, u64, ctypes.POINTER(vp), ctypes.POINTER(InsertInfo)], i32),
+            "dm_server_pause": ([vp, u32, i32], i32),
+            "dm_server_online_view": ([vp, u32, u32, ctypes.POINTER(OnlineView)], i32),
+            "dm_server_online_copy": ([vp, u32, u32, vp, sz, vp, sz, ctypes.POINTER(OnlineView)], i32),
+            "dm_column_digest": ([pin, pout, u32, vp, vp], i32),
+            "dm_online_simulate": ([u32, u32, vp, vp, vp, vp, u64, vp, vp, vp, vp, vp, vp, u64, vp, vp,
+                                    vp, vp, vp, vp, ctypes.POINTER(u64)], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -658,6 +696,21 @@ def fetch(res: DeviceResult, w: int, n_out: int):
     return new_dict, xm, xd, packed, b, u
 
 
+def dm_column_digest(cin: ColumnIn, cout: ColumnOut, col_index: int, d_digest, stream=None):
+    """Add the checksum of a merged column's outputs to the device word d_digest."""
+    _check(_load().dm_column_digest(ctypes.byref(cin), ctypes.byref(cout), col_index, _ptr(d_digest),
+                                    _stream(stream)), "dm_column_digest")
+
+
+def column_digests(cins, couts, stream=None):
+    """One checksum per column (host ints), from dm_column_digest."""
+    import torch
+    acc = torch.zeros(max(len(cins), 1), dtype=torch.int64, device="cuda")
+    for j, (ci, co) in enumerate(zip(cins, couts)):
+        dm_column_digest(ci, co, j, acc[j:j + 1], stream)
+    return [int(x) & (2**64 - 1) for x in acc[:len(cins)].cpu().tolist()]
+
+
 # ------------------------------------------------------------------ served merges
 
 class Server:
@@ -709,6 +762,53 @@ class Server:
     def version(self, table_id: int) -> int:
         return int(_load().dm_server_table_version(self.handle, table_id))
 
+    def add_online_table(self, table_id: int, cols, main_rows: int, rows_capacity: int,
+                         delta_capacity: int, trigger: float = 0.0):
+        """Register a server-owned online table; cols: OnlineColumn structures."""
+        n = len(cols)
+        cfg = OnlineConfig(main_rows, rows_capacity, delta_capacity, float(trigger))
+        _check(_load().dm_server_add_online_table(self.handle, table_id, n, (OnlineColumn * n)(*cols),
+                                                  ctypes.byref(cfg)), "dm_server_add_online_table")
+
+    def insert(self, table_id: int, nrows: int, values) -> InsertInfo:
+        """Append nrows rows; values: one tensor (device) or array per column."""
+        ptrs = (ctypes.c_void_p * max(len(values), 1))(*[_ptr(v) for v in values])
+        info = InsertInfo()
+        _check(_load().dm_server_insert(self.handle, table_id, nrows, ptrs, ctypes.byref(info)),
+               "dm_server_insert")
+        return info
+
+    def pause(self, table_id: int, paused: bool = True):
+        _check(_load().dm_server_pause(self.handle, table_id, 1 if paused else 0), "dm_server_pause")
+
+    def resume(self, table_id: int):
+        self.pause(table_id, False)
+
+    def online_view(self, table_id: int, col: int) -> OnlineView:
+        v = OnlineView()
+        _check(_load().dm_server_online_view(self.handle, table_id, col, ctypes.byref(v)),
+               "dm_server_online_view")
+        return v
+
+    def online_copy(self, table_id: int, col: int, w: int):
+        """The committed version of a column, copied to host memory:
+        (version, U_M keys, packed words, E_C, N_M)."""
+        v = self.online_view(table_id, col)
+        for _ in range(8):
+            kd = key_np_dtype(w)
+            keys = np.zeros((v.main_dict_len, 2) if w == 16 else v.main_dict_len, kd)
+            words = np.zeros(dm_packed_bytes(v.main_rows, 32) // 4 + 4, np.uint32)
+            got = OnlineView()
+            rc = _load().dm_server_online_copy(self.handle, table_id, col, _ptr(keys), keys.nbytes,
+                                               _ptr(words), words.nbytes, ctypes.byref(got))
+            if rc == DM_OK and got.main_dict_len == v.main_dict_len:
+                nw = dm_packed_bytes(got.main_rows, got.main_bits) // 4
+                return int(got.version), keys, words[:nw].copy(), int(got.main_bits), int(got.main_rows)
+            if rc not in (DM_OK, DM_EINVAL):
+                _check(rc, "dm_server_online_copy")
+            v = self.online_view(table_id, col)   # a commit came in between: size again
+        raise DmError(DM_EBUSY, "dm_server_online_copy")
+
     @property
     def tune_cache(self) -> TuneCache:
         """The cache every slot looks its launch choices up in."""
@@ -735,3 +835,38 @@ def dm_sched_simulate(pool_bytes: int, slots: int, footprint, service_ns, req_ta
                                      _ptr(ar), _ptr(admit), _ptr(done), _ptr(slot),
                                      ctypes.byref(pb), ctypes.byref(pr)), "dm_sched_simulate")
     return admit, done, slot, int(pb.value), int(pr.value)
+
+
+def dm_online_simulate(slots: int, main_rows, delta_capacity, trigger, service_ns, ev_kind, ev_table,
+                       ev_rows, ev_ns, max_merges: int = 4096):
+    """The online-table rules on a fake clock (no GPU).  Events: kind 0 insert
+    (ev_rows rows), 1 merge request, 2 pause, 3 resume.  Returns a dict with,
+    per event, 'lands_in' (the version an insert was told) and 'version' (the
+    version whose merge took it), and per merge in admission order 'table',
+    'admit_ns', 'done_ns', 'rows', 'version', 'automatic'."""
+    mr = np.ascontiguousarray(main_rows, np.uint64)
+    dc = np.ascontiguousarray(delta_capacity, np.uint64)
+    tg = np.ascontiguousarray(trigger, np.float64)
+    sv = np.ascontiguousarray(service_ns, np.uint64)
+    ek = np.ascontiguousarray(ev_kind, np.uint32)
+    et = np.ascontiguousarray(ev_table, np.uint32)
+    er = np.ascontiguousarray(ev_rows, np.uint64)
+    en = np.ascontiguousarray(ev_ns, np.uint64)
+    n = ek.size
+    lands = np.zeros(max(n, 1), np.uint64)
+    ver = np.zeros(max(n, 1), np.uint64)
+    mt = np.zeros(max_merges, np.uint32)
+    ma = np.zeros(max_merges, np.uint64)
+    md = np.zeros(max_merges, np.uint64)
+    mrw = np.zeros(max_merges, np.uint64)
+    mv = np.zeros(max_merges, np.uint64)
+    mau = np.zeros(max_merges, np.uint32)
+    nm = ctypes.c_uint64(0)
+    _check(_load().dm_online_simulate(slots, mr.size, _ptr(mr), _ptr(dc), _ptr(tg), _ptr(sv), n, _ptr(ek),
+                                      _ptr(et), _ptr(er), _ptr(en), _ptr(lands), _ptr(ver), max_merges,
+                                      _ptr(mt), _ptr(ma), _ptr(md), _ptr(mrw), _ptr(mv), _ptr(mau),
+                                      ctypes.byref(nm)), "dm_online_simulate")
+    k = min(int(nm.value), max_merges)
+    return {"lands_in": lands[:n], "version": ver[:n], "table": mt[:k], "admit_ns": ma[:k],
+            "done_ns": md[:k], "rows": mrw[:k], "version_of_merge": mv[:k], "automatic": mau[:k],
+            "merges": int(nm.value)}

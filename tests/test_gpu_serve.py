@@ -109,3 +109,36 @@ def test_server_rejects_a_table_larger_than_the_budget():
         srv.add_table(0, [d.cin() for d in dcols], [r.cout() for r in res])
     assert e.value.status == dm.DM_ENOMEM
     srv.close()
+
+
+def test_request_digests_equal_solo_runs_and_change_with_the_result():
+    """DM_SERVER_DIGEST: each request's checksum equals that of its table
+    merged alone, and a column whose result differs has a different one."""
+    import torch
+
+    from paper_1109_6885_gb300 import build
+    build.build()
+    tables = make_tables(5, seed=3)
+    footprints = [dm.dm_table_scratch_bytes([d.cin() for d in t[1]]) for t in tables]
+    srv = dm.Server(0, slots=3, scratch_budget=int(2.5 * max(footprints)), flags=dm.DM_SERVER_DIGEST)
+    for tid, (cols, dcols, res) in enumerate(tables):
+        srv.add_table(tid, [d.cin() for d in dcols], [r.cout() for r in res])
+    solo = []
+    for tid in range(len(tables)):
+        rid = srv.submit(tid)
+        srv.drain()
+        solo.append(srv.info(rid).digest)
+    rids = [(tid, srv.submit(tid)) for _ in range(4) for tid in range(len(tables))]
+    srv.drain()
+    for tid, rid in rids:
+        assert srv.info(rid).digest == solo[tid]
+    assert len(set(solo)) == len(solo)
+    # the same checksum from dm_column_digest, and a flipped output word changes it
+    cols, dcols, res = tables[0]
+    cins, couts = [d.cin() for d in dcols], [r.cout() for r in res]
+    torch.cuda.synchronize()
+    per_col = dm.column_digests(cins, couts)
+    assert sum(per_col) % 2**64 == solo[0]
+    res[0].new_packed[0] ^= 1
+    assert dm.column_digests(cins, couts)[0] != per_col[0]
+    srv.close()
