@@ -42,6 +42,14 @@ WORKLOADS = {
     # the same with 16-byte keys
     "column-100M-k16-zipf1-delta1M": dict(n_main=100_000_000, m=1_000_000, w=16,
                                           n_delta=1_000_000, f_new=0.3, dist="zipf", zipf_s=1.0),
+    # the literal reading of "30% new values": every fresh delta row brings its
+    # own new value (300,000 of them), so U' grows to 1.3M entries at 21 bits
+    "column-100M-u64-zipf1-delta1M-300knew": dict(n_main=100_000_000, m=1_000_000, w=8,
+                                                  n_delta=1_000_000, f_new=0.3, dist="zipf",
+                                                  zipf_s=1.0, pool=0),
+    # a narrow column: 50M rows over 8 distinct 4-byte values (3 bits), 1% delta
+    "column-50M-u32-3bit-delta500k": dict(n_main=50_000_000, m=8, w=4, n_delta=500_000, f_new=0.3,
+                                          dist="zipf", zipf_s=0.8),
     # the same shape at 40% of the rows (for profiler captures: a few GB on the device)
     "column-40M-u64-zipf1-delta400k": dict(n_main=40_000_000, m=400_000, w=8, n_delta=400_000,
                                            f_new=0.3, dist="zipf", zipf_s=1.0),
