@@ -71,6 +71,10 @@ TABLES = {
     # columns would take longer than the run
     "table-300x50M-mixed": dict(ncols=300, n_main=50_000_000, n_delta=500_000, max_m=50_000_000,
                                 distinct=30),
+    # the shape of the sales-document table of Section 2's example: 33M rows,
+    # 230 columns, a 750,000-row delta (column data repeating every 23)
+    "table-230x33M-vbap": dict(ncols=230, n_main=33_000_000, n_delta=750_000, max_m=33_000_000,
+                               distinct=23),
 }
 # served merges: resident tables of 20-60 columns, main rows log-uniform in
 # [100k, 4M], delta 0.1-10% of main; Poisson arrivals at `rate` requests/s
@@ -87,6 +91,13 @@ SERVES = {
     "serve-64tables-poisson20": dict(ntables=64, cols=(20, 200), rows=(100_000, 200_000_000), rate=20.0,
                                      requests=400, slots=4, budget=150 << 30, distinct=2),
 }
+# the single-column sweep: main 100M rows, unique fraction x value width x
+# delta size, 30% of the delta new, uniform codes, minimal widths (each point
+# timed as its own column; --sweep-deltas picks the delta sizes)
+SWEEPS = {
+    "sweep-100M": dict(n_main=100_000_000, unique=(1e-5, 1e-3, 0.1, 1.0), widths=(4, 8, 16),
+                       deltas=(0.001, 0.01, 0.1), f_new=0.3),
+}
 DEFAULT_WORKLOAD = "column-100M-u64-zipf1-delta1M"
 L2_BYTES = 129 * 2**20
 
@@ -98,7 +109,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                   choices=sorted(WORKLOADS) + sorted(TABLES) + sorted(SERVES))
+                   choices=sorted(WORKLOADS) + sorted(TABLES) + sorted(SERVES) + sorted(SWEEPS))
+    p.add_argument("--sweep-deltas", default="0.01",
+                   help="sweep workloads: comma-separated delta sizes as fractions of main (default 0.01)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -942,10 +955,97 @@ def run_serve(args):
         print(json.dumps(line), flush=True)
 
 
+def time_column(dm, ctx, dcol, res, steps, warmup, flush):
+    """Median-free per-kernel timing of `steps` merges of one resident column
+    (L2 flushed before each when `flush` is given): (ms per merge from one
+    event per step, Step 1 ms, Step 2(b) ms, device status)."""
+    import torch
+    cin, cout = dcol.cin(), res.cout()
+    for k in range(max(warmup, 3)):
+        dm.dm_merge_column(ctx, cin, cout, None, dm.DM_FLAG_TIMING if k % 2 else 0)
+    torch.cuda.synchronize()
+    ctx.timing_sum()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        if flush is not None:
+            flush.fill_(k & 0xFF)
+        ev[k][0].record()
+        dm.dm_merge_column(ctx, cin, cout)
+        ev[k][1].record()
+    for k in range(steps):
+        if flush is not None:
+            flush.fill_(k & 0xFF)
+        dm.dm_merge_column(ctx, cin, cout, None, dm.DM_FLAG_TIMING)
+    torch.cuda.synchronize()
+    ms, calls = ctx.timing_sum()
+    whole = sum(a.elapsed_time(b) for a, b in ev) / steps
+    return whole, (ms[0] + ms[1] + ms[2]) / max(calls, 1), ms[3] / max(calls, 1), ctx.sync_status()
+
+
+def run_sweep(args):
+    """The single-column sweep (unique fraction x value width x delta size):
+    one JSON line with every point's merged tuples/s, the re-encode's
+    fraction of measured HBM bandwidth and the Step 1 / Step 2(b) split."""
+    import torch
+
+    from paper_1109_6885_gb300 import build
+    from paper_1109_6885_gb300 import dmerge as dm
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    build.build()
+    dm.load()
+    cfg = SWEEPS[args.workload]
+    deltas = [float(x) for x in args.sweep_deltas.split(",")]
+    peak, peak_kind = measured_peaks()
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+    points = []
+    sampler = ClockSampler(local, not args.no_clocks)
+    sampler.wait_ready()
+    for j, (lam, w, fd) in enumerate([(l, w, f) for l in cfg["unique"] for w in cfg["widths"] for f in deltas]):
+        n_main = cfg["n_main"]
+        m = max(1, int(round(lam * n_main)))
+        if w == 4 and m > 2**31:
+            continue
+        spec = synth.ColumnSpec(n_main=n_main, m=m, w=w, n_delta=int(fd * n_main), f_new=cfg["f_new"],
+                                dist="uniform", seed=synth.column_seed(3, j))
+        col = synth.make_column(spec)
+        ctx = dm.Context(local)
+        dcol = dm.DeviceColumn.from_numpy(col.w, col.main_dict, col.main_packed, col.main_bits, col.n_main,
+                                          col.delta_dict, col.delta_codes)
+        res = dm.alloc_result(dcol, with_x=False)
+        ctx.reserve(dm.dm_scratch_bytes(dcol.cin()))
+        whole, s1, s2, st = time_column(dm, ctx, dcol, res, args.steps, args.warmup, flush)
+        u, b_new = res.u_bits()
+        d = col.delta_dict.shape[0]
+        step2 = traffic.step2_bytes(col.main_bits, b_new, col.n_main, col.n_delta, m, d)
+        n = col.n_main + col.n_delta
+        points.append({"unique": lam, "value_bytes": w, "delta": fd, "dict_main": m, "dict_delta": d,
+                       "dict_new": u, "bits_in": col.main_bits, "bits_out": b_new,
+                       "tuples_per_s": n / (whole / 1e3), "ms_per_merge": whole, "step1_ms": s1,
+                       "reencode_ms": s2, "reencode_frac_of_hbm": step2 / (s2 / 1e3) / 1e9 / peak,
+                       "status": st})
+        ctx.close()
+        del dcol, res, col
+        torch.cuda.empty_cache()
+    clocks = sampler.stop()
+    line = {"metric": "merged tuples/s per column (sweep)", "value": min(p["tuples_per_s"] for p in points),
+            "unit": "tuples/s", "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64/u128",
+            "data": "synthetic", "config": {"workload": args.workload, **{k: v for k, v in cfg.items()},
+                                            "deltas": deltas, "l2": "L2 flushed before every merge"},
+            "peak_gbs": peak, "peak_source": peak_kind, "points": points, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in SWEEPS:
+        run_sweep(args)
     elif args.workload in TABLES:
         run_table(args)
     elif args.workload in SERVES:
