@@ -116,7 +116,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--ingest", action="store_true",
-                   help="column workloads: also time delta ingest (Section 4) of the workload's delta rows")
+                   help="column and table workloads: also time delta ingest (Section 4) of the workload's delta "
+                        "rows and report the update rate N_D / (T_U + T_M)")
     p.add_argument("--unopt", action="store_true",
                    help="column workloads: also time Step 2(b) by binary search in U' (Section 5.2) against the "
                         "translation tables")
@@ -493,8 +494,14 @@ def run_gpu(args):
         dl = int(igl.item())
         same = dl == dcol.d and bool(torch.equal(igd[:dl], dcol.delta_dict)) and \
             bool(torch.equal(igc[:nd], dcol.delta_codes))
+        # the update rate of Eq. 1 / Eq. 16: the delta's rows over the time
+        # to insert them (T_U, the ingest) plus the time to merge them (T_M)
+        merge_ms = total_ms / args.steps
         ingest = {"rows": nd, "ms": ims, "rows_per_s": nd / (ims / 1e3), "dict": dl,
-                  "same_as_the_workload_delta": same, "status": ctx.sync_status()}
+                  "same_as_the_workload_delta": same, "status": ctx.sync_status(),
+                  "update_rate": {"updates_per_s": nd / ((ims + merge_ms) / 1e3), "t_u_ms": ims,
+                                  "t_m_ms": merge_ms, "definition": "N_D / (T_U + T_M), Eq. 1 and Eq. 16, "
+                                                                     "one column"}}
 
     unopt = None
     if args.unopt:
@@ -741,6 +748,38 @@ def run_table(args):
                   "status": ctx.sync_status(), "check": "dm_column_digest of U', E'_C and the packed codes"}
     if tune is not None:
         tune["speedup_vs_defaults"] = tune["defaults_ms_per_step"] / (t_batched / args.steps)
+    update = None
+    if args.ingest:
+        # Eq. 16's update rate for the table: its N_D delta rows over the time
+        # to insert them into every column (T_U: each column's delta ingest,
+        # columns with repeated data timed once) plus the batched merge (T_M)
+        per_src = {}
+        for j in mine:
+            k = j % nsrc
+            if k in per_src:
+                continue
+            d = srcs[k][1]
+            vals = d.delta_dict[d.delta_codes.long()]
+            nd = int(d.n_delta)
+            igd = dm.key_tensor_empty(max(nd, 1), d.w)
+            igc = torch.empty(max(nd, 1), dtype=torch.int32, device=f"cuda:{local}")
+            igl = torch.zeros(1, dtype=torch.int64, device=f"cuda:{local}")
+            ictx_need = dm.dm_ingest_scratch_bytes(d.w, nd)
+            if ictx_need > ctx.arena_bytes:
+                ctx.reserve(ictx_need)
+            dm.dm_ingest_delta(ctx, d.w, vals, nd, igd, igc, igl, stream)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+            for a_, b_ in ev:
+                a_.record(stream)
+                dm.dm_ingest_delta(ctx, d.w, vals, nd, igd, igc, igl, stream)
+                b_.record(stream)
+            torch.cuda.synchronize()
+            per_src[k] = sorted(a_.elapsed_time(b_) for a_, b_ in ev)[2]
+        t_u = sum(per_src[j % nsrc] for j in mine)
+        t_m = t_batched / args.steps
+        n_d = TABLES[args.workload]["n_delta"]
+        update = {"updates_per_s": n_d / ((t_u + t_m) / 1e3), "t_u_ms": t_u, "t_m_ms": t_m, "columns": len(mine),
+                  "definition": "N_D / (T_U + T_M), Eq. 16: T_U every column's delta ingest, T_M the batched merge"}
     step2 = 0
     for c, r in zip(cols, res):
         u, b = r.u_bits()
@@ -772,6 +811,8 @@ def run_table(args):
             line["autotune"] = tune
         if verify is not None:
             line["verify"] = verify
+        if update is not None:
+            line["update_rate"] = update
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -656,3 +656,39 @@ def test_directory_mode_flags_codes_past_the_dictionary(ctx):
     got = np.array(_brute.unpack_bits(dm.to_host(out, np.uint32)[:2000], 1000, b))
     want = np.minimum(mc[:1000], m - 1)
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("n_hi", [1, 7])
+def test_k16_keys_sharing_hi_words_at_scale(ctx, n_hi):
+    """16-byte keys whose hi words take only n_hi values (1: all equal), so
+    that sorting, merging and deduplication decide on the lo words: 1.4M
+    main values, a 300k-row delta of which half repeat main values, 3M main
+    rows."""
+    rng = np.random.default_rng(160 + n_hi)
+    his = np.unique(rng.integers(0, 2**62, 4 * n_hi, dtype=np.uint64))[:n_hi]
+    his = his[rng.permutation(his.size)][:n_hi]
+    his.sort()
+    per = 1_400_000 // n_hi
+    groups = []
+    for g, h in enumerate(his):
+        lo = synth.dictionary(synth.subseed(17, g), 8, per)
+        groups.append(np.stack([np.full(per, h, np.uint64), lo], axis=1))
+    um = np.concatenate(groups)
+    m = um.shape[0]
+    n_main, n_delta = 3_000_000, 300_000
+    mc = rng.integers(0, m, n_main).astype(np.uint32)
+    fresh = np.stack([his[rng.integers(0, n_hi, n_delta)], rng.integers(0, 2**63, n_delta, dtype=np.uint64)],
+                     axis=1)
+    rows = np.where((rng.random(n_delta) < 0.5)[:, None], um[rng.integers(0, m, n_delta)], fresh)
+    # insertion-order dictionary of the delta rows and their codes
+    _, first, inv = np.unique(rows, axis=0, return_index=True, return_inverse=True)
+    order = np.argsort(first)
+    dd = rows[first[order]]
+    rank = np.empty_like(order)
+    rank[order] = np.arange(order.size)
+    dc = rank[inv.reshape(-1)].astype(np.uint32)
+    b = synth.bits_for(m)
+    spec = synth.ColumnSpec(n_main=n_main, m=m, w=16, n_delta=n_delta)
+    col = synth.Column(spec, np.ascontiguousarray(um), mc, b, synth.pack(mc, b), np.ascontiguousarray(dd), dc)
+    ref = assert_parity(ctx, col)
+    assert ref.u > m
