@@ -8,8 +8,9 @@
 // GPU form:
 //   1. a hash table of row indices: each slot holds the smallest row of one
 //      value (the row is the key's representative, so any width needs only
-//      32-bit atomics: claim an empty slot with a CAS, or lower the row of a
-//      slot whose representative equals the value with atomicMin);
+//      32-bit atomics: a row reads the slot, claims it with a CAS if it is
+//      empty, or lowers its row with atomicMin if its representative
+//      equals the value and is a later row);
 //      open addressing, linear probing, load at most one half;
 //      a row's slot is final once it claims it or finds its value there,
 //      so the insert also records each row's slot;
@@ -39,6 +40,8 @@ constexpr uint32_t IG_PER_THREAD = 4;
 constexpr uint32_t IG_TILE = IG_THREADS * IG_PER_THREAD;   // rows per tile
 constexpr uint32_t IG_EMPTY = 0xFFFFFFFFu;
 constexpr uint64_t IG_MAX_ROWS = 1ull << 30;
+constexpr uint32_t IG_CACHE = 2048;                      // block cache entries (16 KiB)
+constexpr uint64_t IG_CACHE_EMPTY = ~0ull;
 
 // Table slots for n rows: a power of two of at least 2n (and 64).
 uint64_t table_slots(uint64_t n) {
@@ -83,32 +86,84 @@ struct IngestArgs {
   uint32_t* status;
 };
 
+// Lanes of the warp holding the same key as this lane.
+__device__ __forceinline__ uint32_t match_key(uint32_t v) { return __match_any_sync(0xFFFFFFFFu, v); }
+__device__ __forceinline__ uint32_t match_key(uint64_t v) {
+  return __match_any_sync(0xFFFFFFFFu, (unsigned long long)v);
+}
+__device__ __forceinline__ uint32_t match_key(const u128& v) {
+  return __match_any_sync(0xFFFFFFFFu, (unsigned long long)v.hi) &
+         __match_any_sync(0xFFFFFFFFu, (unsigned long long)v.lo);
+}
+
+// Block-local cache entries, (row << 32) | slot, read and written whole.
+__device__ __forceinline__ uint64_t cache_ld(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.cta.shared.b64 %0, [%1];" : "=l"(v) : "r"((uint32_t)__cvta_generic_to_shared(p)));
+  return v;
+}
+__device__ __forceinline__ void cache_st(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.cta.shared.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(p)), "l"(v)
+               : "memory");
+}
+
+// One block-stride round of 256 rows per block.  The lanes of a warp that
+// hold one value elect the lowest (its smallest row); only it looks the value
+// up, and the others take its slot.  The leader looks first in the block's
+// cache of recent (row, slot) pairs: an entry is right for the value when the
+// value of its row equals it (a slot keeps its value for good), and the
+// slot's row is then at most the entry's row (rows only decrease), so
+// atomicMin is needed only for a smaller row.  A frequent value thus reaches
+// the table about once per block instead of once per warp.  Otherwise it
+// probes the table, reading each slot before any atomic.
 template <int W>
 __global__ void __launch_bounds__(IG_THREADS) ingest_insert_kernel(IngestArgs a) {
   using K = typename KeyOf<W>::T;
+  __shared__ uint64_t cache[IG_CACHE];
+  for (uint32_t i = threadIdx.x; i < IG_CACHE; i += IG_THREADS) cache[i] = IG_CACHE_EMPTY;
+  __syncthreads();
   const K* vals = static_cast<const K*>(a.values);
   const uint64_t mask = a.slots - 1;
-  for (uint64_t r = (uint64_t)blockIdx.x * IG_THREADS + threadIdx.x; r < a.n; r += (uint64_t)gridDim.x * IG_THREADS) {
-    const K v = load_key(vals + r);
-    uint64_t s = hash_key(v) & mask;
-    bool placed = false;
-    for (uint64_t p = 0; p < a.slots; ++p, s = (s + 1) & mask) {
-      uint32_t cur = atomicCAS(a.table + s, IG_EMPTY, (uint32_t)r);
-      if (cur == IG_EMPTY) {
-        placed = true;   // claimed
-        break;
-      }
-      if (key_eq(load_key(vals + cur), v)) {
-        atomicMin(a.table + s, (uint32_t)r);
-        placed = true;
-        break;
+  const uint32_t lane = threadIdx.x & 31;
+  for (uint64_t base = (uint64_t)blockIdx.x * IG_THREADS; base < a.n; base += (uint64_t)gridDim.x * IG_THREADS) {
+    const uint64_t r = base + threadIdx.x;
+    const bool valid = r < a.n;
+    const K v = load_key(vals + (valid ? r : base));
+    const uint32_t group = match_key(v) & __ballot_sync(0xFFFFFFFFu, valid);
+    const uint32_t leader = group ? (uint32_t)(__ffs(group) - 1) : lane;
+    uint32_t slot = IG_EMPTY;
+    if (valid && leader == lane) {
+      const uint32_t h = hash_key(v);
+      uint64_t* ce = cache + ((h >> 11) & (IG_CACHE - 1));
+      const uint64_t e = cache_ld(ce);
+      if (e != IG_CACHE_EMPTY && key_eq(load_key(vals + (uint32_t)(e >> 32)), v)) {
+        slot = (uint32_t)e;
+        if ((uint32_t)r < (uint32_t)(e >> 32)) atomicMin(a.table + slot, (uint32_t)r);
+      } else {
+        uint64_t s = h & mask;
+        for (uint64_t p = 0; p < a.slots; ++p, s = (s + 1) & mask) {
+          uint32_t cur = __ldcg(a.table + s);
+          if (cur == IG_EMPTY) {
+            cur = atomicCAS(a.table + s, IG_EMPTY, (uint32_t)r);
+            if (cur == IG_EMPTY) {   // claimed
+              slot = (uint32_t)s;
+              cache_st(ce, ((uint64_t)r << 32) | s);
+              break;
+            }
+          }
+          if (key_eq(load_key(vals + cur), v)) {
+            if ((uint32_t)r < cur) atomicMin(a.table + s, (uint32_t)r);
+            slot = (uint32_t)s;
+            cache_st(ce, ((uint64_t)min((uint32_t)r, cur) << 32) | s);
+            break;
+          }
+        }
       }
     }
-    if (placed) {
-      a.slot_of[r] = (uint32_t)s;
-    } else {
-      flag_status(a.status, ST_INTERNAL);   // cannot happen at load <= 1/2
-      a.slot_of[r] = IG_EMPTY;
+    slot = __shfl_sync(0xFFFFFFFFu, slot, leader);
+    if (valid) {
+      if (slot == IG_EMPTY) flag_status(a.status, ST_INTERNAL);   // cannot happen at load <= 1/2
+      a.slot_of[r] = slot;
     }
   }
 }
