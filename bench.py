@@ -57,6 +57,10 @@ WORKLOADS = {
     # (10M values, 24 bits), delta 1% of main (host generation takes minutes)
     "column-1B-u64-uniq1pct-delta1pct": dict(n_main=1_000_000_000, m=10_000_000, w=8, n_delta=10_000_000,
                                              f_new=0.3, dist="uniform"),
+    # Figure 8's 100%-unique corner: 100M rows over 100M uint64 values (27
+    # bits), delta 1% of main; X_M (400 MB) is larger than L2
+    "column-100M-u64-uniq100pct-delta1pct": dict(n_main=100_000_000, m=100_000_000, w=8, n_delta=1_000_000,
+                                                 f_new=0.3, dist="uniform"),
     # 1M-row column over 100k uniform uint64 values at 17 bits, 10k-row delta, half new
     "column-1M-u64-delta10k": dict(n_main=1_000_000, m=100_000, w=8, n_delta=10_000, f_new=0.5,
                                    dist="uniform", pool=0),
