@@ -954,6 +954,146 @@ __device__ void merge_tile(const Step1Args& a, uint32_t tile, const typename Key
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- small dictionaries
+// Steps 1(a), 1(b) and 2(a) of a column whose dictionaries are small (at most
+// SM_MAX_M main and SM_MAX_D delta entries) by one block with a short code
+// path.  The tiled kernel spends 20-35 us on such a column whatever its size:
+// its phases and grid barriers run once through a long, cold instruction
+// stream.  Here both dictionaries sit in shared memory and every code comes
+// from binary searches:
+//   * each delta value is ranked in U_M; the values not in U_M (the new
+//     values of U') are gathered, sorted (bitonic) and counted once each;
+//   * with q(x) the number of distinct new values below x, U_M[i] takes code
+//     i + q(U_M[i]), a distinct new value v takes #{U_M < v} + q(v), and
+//     delta entry j takes #{U_M < D[j]} + q(D[j]) (U' is the sorted union
+//     without duplicates, Eq. 3; X_M and X_D give each value's position in
+//     it, Section 5.3).
+// Repeated delta values get one code; a U_M that is not strictly increasing
+// is flagged as the tiled kernel flags it.  No wait, no look-back.
+constexpr uint32_t SM_MAX_M = 4096, SM_MAX_D = 2048;
+
+template <int W>
+constexpr size_t small_smem_bytes() {
+  return (size_t)(SM_MAX_M + 2 * SM_MAX_D) * W + (size_t)(2 * SM_MAX_D + 1 + S1_WARPS) * 4;
+}
+
+// First index of s[0..n) whose key is not below x (lower) or above x (upper).
+template <class K>
+__device__ __forceinline__ uint32_t bound_s(const K* s, uint32_t n, const K& x, bool upper) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (upper ? !key_lt(x, s[mid]) : key_lt(s[mid], x)) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Exclusive scan of flag(k), k < n <= SM_MAX_D, into out[0..n]; returns the
+// total (out[n]).  Every thread takes a run of consecutive k.
+template <class F>
+__device__ __forceinline__ uint32_t small_scan(uint32_t n, F flag, uint32_t* out, uint32_t* wsum) {
+  constexpr uint32_t PER = SM_MAX_D / S1_THREADS;
+  const uint32_t k0 = threadIdx.x * PER;
+  uint32_t f[PER], sum = 0;
+#pragma unroll
+  for (uint32_t q = 0; q < PER; ++q) {
+    f[q] = k0 + q < n ? flag(k0 + q) : 0u;
+    sum += f[q];
+  }
+  uint32_t total = 0;
+  uint32_t ex = block_excl_scan(sum, wsum, &total);
+#pragma unroll
+  for (uint32_t q = 0; q < PER; ++q) {
+    if (k0 + q < n) out[k0 + q] = ex;
+    ex += f[q];
+  }
+  if (threadIdx.x == 0) out[n] = total;
+  __syncthreads();
+  return total;
+}
+
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS) step1_small_kernel(Step1Args a) {
+  using K = typename KeyOf<W>::T;
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  K* sA = reinterpret_cast<K*>(smem_raw);
+  K* sD = sA + SM_MAX_M;
+  K* sN = sD + SM_MAX_D;
+  uint32_t* lbm = reinterpret_cast<uint32_t*>(sN + SM_MAX_D);   // #{U_M < D[j]}, bit 31: D[j] is new
+  uint32_t* q = lbm + SM_MAX_D;                                  // scans, SM_MAX_D + 1 words
+  uint32_t* wsum = q + SM_MAX_D + 1;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t m = (uint32_t)a.m, d = (uint32_t)a.d;
+  const K* A = static_cast<const K*>(a.a);
+  const K* D = static_cast<const K*>(a.in_keys);
+  for (uint32_t i = tid; i < m; i += S1_THREADS) sA[i] = load_key(A + i);
+  for (uint32_t j = tid; j < d; j += S1_THREADS) sD[j] = load_key(D + j);
+  __syncthreads();
+  bool unsorted = false;
+  for (uint32_t i = tid + 1; i < m; i += S1_THREADS) unsorted |= !key_lt(sA[i - 1], sA[i]);
+  if (unsorted) flag_status(a.status, ST_UNSORTED);
+  for (uint32_t j = tid; j < d; j += S1_THREADS) {
+    const uint32_t r = bound_s(sA, m, sD[j], true);
+    const bool in_main = r > 0 && key_eq(sA[r - 1], sD[j]);
+    lbm[j] = in_main ? r - 1 : (r | 0x80000000u);
+  }
+  __syncthreads();
+  // the new values, gathered in delta order, then sorted (padded with the
+  // largest key to a power of two; only the first nn are read)
+  const uint32_t nn = small_scan(d, [&](uint32_t j) { return lbm[j] >> 31; }, q, wsum);
+  for (uint32_t j = tid; j < d; j += S1_THREADS)
+    if (lbm[j] >> 31) sN[q[j]] = sD[j];
+  uint32_t np = 1;
+  while (np < nn) np <<= 1;
+  for (uint32_t k = nn + tid; k < np; k += S1_THREADS) sN[k] = key_max_value<K>();
+  __syncthreads();
+  for (uint32_t k = 2; k <= np; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = tid; i < np; i += S1_THREADS) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+          const K x = sN[i], y = sN[l];
+          if ((i & k) == 0 ? key_lt(y, x) : key_lt(x, y)) {
+            sN[i] = y;
+            sN[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // q[k]: distinct new values among sN[0..k)
+  const uint32_t nd = small_scan(nn, [&](uint32_t k) { return k == 0 || !key_eq(sN[k - 1], sN[k]) ? 1u : 0u; },
+                                 q, wsum);
+  const uint32_t u = m + nd;
+  K* unew = static_cast<K*>(a.unew);
+  for (uint32_t i = tid; i < m; i += S1_THREADS) {
+    const uint32_t code = i + q[bound_s(sN, nn, sA[i], false)];
+    if (code < u) {
+      unew[code] = sA[i];
+      a.xm[i] = code;
+    } else {
+      flag_status(a.status, ST_INTERNAL);
+    }
+  }
+  for (uint32_t k = tid; k < nn; k += S1_THREADS) {
+    if (k > 0 && key_eq(sN[k - 1], sN[k])) continue;
+    const uint32_t code = bound_s(sA, m, sN[k], false) + q[k];
+    if (code < u) unew[code] = sN[k];
+    else flag_status(a.status, ST_INTERNAL);
+  }
+  for (uint32_t j = tid; j < d; j += S1_THREADS) {
+    const uint32_t code = (lbm[j] & 0x7FFFFFFFu) + q[bound_s(sN, nn, sD[j], false)];
+    if (code < u) a.xd[j] = code;
+    else flag_status(a.status, ST_INTERNAL);
+  }
+  if (tid == 0) {
+    *a.d_u = u;
+    *a.d_bits = bits_for(u);
+  }
+}
+
 // ---------------------------------------------------------------- the kernel
 template <int W>
 __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
@@ -1249,6 +1389,9 @@ int prepare_w(cudaError_t* err) {
                          (const void*)step1_pass_kernel<W>, (const void*)step1_msd_kernel<W>,
                          (const void*)step1_bucket_kernel<W>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step1_small_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)small_smem_bytes<W>());
   int per_sm = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step1_kernel<W>, S1_THREADS, smem);
   *err = e;
@@ -1266,6 +1409,15 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
   const int per_sm = prepare_w<W>(&pe);
   if (pe != cudaSuccess) return pe;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  // small dictionaries: one block (not with the wait-test setting, which
+  // needs the tiled kernel's look-back)
+  const bool merge_only_dir = !(a.phases & S1_DIR) || a.dir_entries == 0;
+  if ((a.phases & S1_MERGE) && merge_only_dir && (a.d == 0 || (a.phases & S1_SORT)) && a.m <= SM_MAX_M &&
+      a.d <= SM_MAX_D && a.m + a.d > 0 && a.test_withhold == 0) {
+    step1_small_kernel<W><<<1, S1_THREADS, small_smem_bytes<W>(), s>>>(a);
+    ++*launches;
+    return cudaGetLastError();
+  }
   const uint64_t full = (uint64_t)per_sm * sm_count;
   uint64_t cap = full;
   if (a.grid_cap && a.grid_cap < cap) cap = a.grid_cap;

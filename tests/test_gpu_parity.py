@@ -692,3 +692,41 @@ def test_k16_keys_sharing_hi_words_at_scale(ctx, n_hi):
     col = synth.Column(spec, np.ascontiguousarray(um), mc, b, synth.pack(mc, b), np.ascontiguousarray(dd), dc)
     ref = assert_parity(ctx, col)
     assert ref.u > m
+
+
+@pytest.mark.parametrize("w,m,d,frac_new,repeats", [
+    (4, 4096, 2048, 1.0, False), (8, 4096, 2048, 0.3, False), (16, 4096, 2048, 0.5, True),
+    (8, 4097, 2048, 0.3, False), (8, 4096, 2049, 0.3, False), (16, 1, 1, 1.0, False),
+    (4, 0, 2048, 1.0, True), (8, 4096, 0, 0.0, False), (8, 1000, 2048, 0.0, True),
+    (16, 2, 2048, 0.999, True), (4, 7, 9, 0.3, False), (8, 4096, 1, 1.0, False)])
+def test_small_dictionaries_at_and_past_the_one_block_limits(ctx, w, m, d, frac_new, repeats):
+    """Dictionaries of at most 4,096 main and 2,048 delta entries take Step 1
+    in one block; one entry more takes the tiled kernel.  Both sides of each
+    limit, all-new and no-new deltas, repeated delta values, an empty main
+    or delta dictionary and 16-byte keys over several hi words."""
+    rng = np.random.default_rng(1000 * w + m + d)
+    his = [0] if w < 16 else [0, 3, 2**64 - 1]
+    span = 2 ** (8 * min(w, 8)) - 1
+    vals = set()
+    while len(vals) < m + d:
+        lo = int(rng.integers(0, span, dtype=np.uint64, endpoint=True))
+        vals.add((int(his[int(rng.integers(0, len(his)))]) << 64) | lo if w == 16 else lo)
+    vals = list(vals)
+    rng.shuffle(vals)
+    um = sorted(vals[:m])
+    fresh = vals[m:]
+    dd = []
+    for k in range(d):
+        if m == 0 or rng.random() < frac_new:
+            dd.append(fresh[int(rng.integers(0, len(fresh)))] if repeats else fresh[k])
+        else:
+            dd.append(um[int(rng.integers(0, m))])
+    if not repeats:
+        dd = list(dict.fromkeys(dd))
+        while len(dd) < d:                     # refill with unused fresh values
+            dd.append(next(v for v in fresh if v not in set(dd)))
+    main_codes = rng.integers(0, m, 20_000).tolist() if m else []
+    dcodes = rng.integers(0, d, 5000).tolist() if d else []
+    col = column_from_lists(w, um, main_codes, dd, dcodes)
+    ref = assert_parity(ctx, col)
+    assert ref.u == len(set(um) | set(dd))
