@@ -46,6 +46,11 @@ constexpr uint64_t RE_X8_MIN_CODES = 8u << 20;
 // Input widths that can carry that many codes (the byte-table path is
 // compiled into their kernels only).
 constexpr bool RE_X8_B(int b) { return (1ull << b) > RE_X8_MIN_CODES; }
+// Input widths whose columns can have more main codes than the direct table
+// holds; only their kernels carry the directory lookup.  Without it a
+// kernel fits 64 registers a thread, so two blocks can share an SM.
+constexpr bool RE_DIR_B(int b) { return (1ull << b) > RE_XSMEM_MAX; }
+constexpr int RE_BLOCKS_MIN(int b) { return RE_DIR_B(b) ? 1 : 2; }
 
 template <int B>
 __device__ __forceinline__ void load_row(const uint32_t* row, uint32_t (&w)[B > 0 ? B : 1]) {
@@ -191,7 +196,7 @@ __global__ void xdir_build_kernel(const uint32_t* __restrict__ xm, uint32_t m, u
 }
 
 template <int B>
-__global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArgs a, Layout L) {
+__global__ void __launch_bounds__(RE_WARPS_MAX * 32, RE_BLOCKS_MIN(B)) reencode_kernel(ReencodeArgs a, Layout L) {
   extern __shared__ __align__(128) uint8_t smem[];
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem) + warp * RE_STAGES_MAX;
@@ -284,7 +289,7 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32) reencode_kernel(ReencodeArg
 #pragma unroll
         for (int j = 0; j < 32; ++j) c[j] = min(c[j], a.m - 1);
       }
-      if (xmode == 2) {
+      if (RE_DIR_B(B) && xmode == 2) {
         uint32_t many = 0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -509,7 +514,8 @@ cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, 
   if (allow_smem && want_smem && a.m <= RE_XSMEM_MAX) {
     L.x_mode = 1;
     L.x_entries = a.m;
-  } else if (allow_smem && want_smem && a.xdir && (uint64_t)a.m <= ((uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX)) {
+  } else if (allow_smem && want_smem && a.xdir && RE_DIR_B((int)b) &&
+             (uint64_t)a.m <= ((uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX)) {
     L.x_mode = 2;
     xdir_shape(a.m, &L.dir_shift, &L.x_entries);
   }
