@@ -322,6 +322,23 @@ def cpu_oracle_rate(col, budget_s: float = 20.0):
     return n * done / el, done, el
 
 
+def cpu_oracle_columns_rate(cols, budget_s: float = 25.0):
+    """The oracle as it stands, one host core, over whole-column merges of
+    `cols` in order until the budget is spent (at least one): tuple-columns/s,
+    columns merged, seconds."""
+    import oracle
+    done, tuples, el = 0, 0, 0.0
+    for col in cols:   # a generator may build each column here, outside the timing
+        t0 = time.perf_counter()
+        oracle.merge_synth_column(col)
+        el += time.perf_counter() - t0
+        done += 1
+        tuples += col.n_main + col.n_delta
+        if el > budget_s:
+            break
+    return tuples / el, done, el
+
+
 def sample_column(col, rows: int):
     """The first `rows` main rows with the whole dictionaries and delta."""
     if rows >= col.n_main:
@@ -784,6 +801,17 @@ def run_table(args):
         n_d = TABLES[args.workload]["n_delta"]
         update = {"updates_per_s": n_d / ((t_u + t_m) / 1e3), "t_u_ms": t_u, "t_m_ms": t_m, "columns": len(mine),
                   "definition": "N_D / (T_U + T_M), Eq. 16: T_U every column's delta ingest, T_M the batched merge"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # every distinct column data set once: the table repeats each of them
+        # equally often, so the oracle's rate over them is its rate on the table
+        distinct = [srcs[k][0] for k in sorted(srcs)]
+        rate, ncols_done, el = cpu_oracle_columns_rate(distinct)
+        cpu = {"value": rate, "unit": "tuple-columns/s", "cores": 1, "kind": "oracle",
+               "sample": f"{ncols_done} of the table's {len(distinct)} distinct columns merged once each "
+                         f"({el:.1f} s, one thread); the {len(specs)} columns repeat them equally often, "
+                         "so the rate is extrapolated to the table unchanged",
+               "host": host_cpu()}
     step2 = 0
     for c, r in zip(cols, res):
         u, b = r.u_bits()
@@ -817,6 +845,7 @@ def run_table(args):
             line["verify"] = verify
         if update is not None:
             line["update_rate"] = update
+        line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:
@@ -916,7 +945,7 @@ def run_serve(args):
     build.build()
     dm.load()
     cfg = SERVES[args.workload]
-    tables, keep, _ = serve_tables(dm, cfg, rank)
+    tables, keep, specs = serve_tables(dm, cfg, rank)
     rng = np.random.default_rng(0x5E7E + rank + 1)
     table_tuples = [int(sum(ci.main_rows + ci.delta_rows for ci in c)) for c, _ in tables]
     nreq = max(args.steps * 10, cfg["requests"])
@@ -977,6 +1006,18 @@ def run_serve(args):
                       "peak_concurrency": r["peak_concurrency"]})
     plain = arm(1, dm.DM_FLAG_SERIAL, False)
     verify = serve_verify(dm, tables, cfg, slot_counts[0], served_flags, tabs, gaps, local) if args.verify else None
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # a seeded sample of the tables' distinct column data sets, each
+        # generated on the host and merged once by the oracle
+        flat = [sp for _, sps in specs for sp in sps]
+        pick = np.random.default_rng(0xC0DE).permutation(len(flat))[:48]
+        rate, ncols_done, el = cpu_oracle_columns_rate((synth.make_column(flat[i]) for i in pick), budget_s=15.0)
+        cpu = {"value": rate, "unit": "tuple-columns/s", "cores": 1, "kind": "oracle",
+               "sample": f"{ncols_done} seeded columns of the {len(flat)} distinct column data sets, merged once "
+                         f"each ({el:.1f} s of merging, one thread); rate over those columns, extrapolated to "
+                         "the served mix",
+               "host": host_cpu()}
     if rank == 0:
         line = {
             "metric": "served merged tuple-columns/s; p50/p99 merge latency", "value": served["value"],
@@ -996,6 +1037,7 @@ def run_serve(args):
                       "slowest": plain["slowest"]},
             **({"slots_sweep": sweep} if sweep else {}),
             **({"verify": verify} if verify else {}),
+            "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
 
