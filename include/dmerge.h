@@ -83,7 +83,8 @@ typedef enum {
 /* flags for dm_merge_column / dm_merge_table */
 #define DM_FLAG_GENERIC_REENCODE 0x1u  /* force the runtime-width Step 2(b) path */
 #define DM_FLAG_X_SMEM 0x2u            /* look X_M up in shared memory at any size (table or directory) */
-#define DM_FLAG_X_GLOBAL 0x4u          /* never stage X_M in shared memory */
+#define DM_FLAG_X_GLOBAL 0x4u          /* gather X_M directly: no shared-memory table or directory, no
+                                          global directory */
 #define DM_FLAG_TIMING 0x8u            /* record per-step CUDA events (dm_last_timing) */
 #define DM_FLAG_SERIAL 0x10u           /* dm_merge_table: one column after another, plain launches */
 #define DM_FLAG_NO_GRAPH 0x40u         /* dm_merge_table: the batched schedule issued directly on the
@@ -196,7 +197,11 @@ dm_status dm_merge_dicts(dm_ctx* ctx, uint32_t value_bytes, const void* main_dic
  * out code n_main + r = x_delta[delta_codes[r]], packed at the width read
  * from the device scalar *d_bits (which must be <= max_bits; the output
  * buffer holds dm_packed_bytes(n_main + n_delta, max_bits) bytes).  Table
- * entries must be < 2^(*d_bits). */
+ * entries must be < 2^(*d_bits).  The context's arena holds the lookup
+ * structures built on the way when it has room for them: the 64 KiB
+ * directory of X_M's steps, then its byte table (m bytes, above 2^23 main
+ * codes) or, above 2^24 main codes, the global directory (8 bytes per 2^s
+ * codes, s >= 6, at most 16 MiB); without room X_M is gathered directly. */
 dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bits,
                       uint64_t n_main, const uint32_t* delta_codes, uint64_t n_delta,
                       const uint32_t* x_main, uint64_t m, const uint32_t* x_delta, uint64_t d,
@@ -537,7 +542,7 @@ typedef struct {
 
 #define DM_STAGE_AUTO 0u     /* X_M lookup: library rule (shared memory from 2^20 main rows) */
 #define DM_STAGE_SMEM 1u     /* X_M in shared memory (table or directory of its steps) when it fits */
-#define DM_STAGE_GLOBAL 2u   /* X_M gathered through L1/L2 */
+#define DM_STAGE_GLOBAL 2u   /* X_M gathered through L1/L2 (no directory of its steps) */
 #define DM_X8_AUTO 0u        /* byte table for crowded directory buckets above 2^23 main codes */
 #define DM_X8_OFF 1u         /* no byte table: crowded buckets read X_M */
 

@@ -47,6 +47,7 @@ struct ColumnScratch {
   uint32_t* xd = nullptr;
   uint32_t* xdir = nullptr;   // directory of X_M for Step 2(b)
   uint8_t* x8 = nullptr;      // its byte table
+  uint2* gdir = nullptr;      // global directory (more main codes than the shared one covers)
   void** slots = nullptr;
 };
 
@@ -66,6 +67,8 @@ size_t carve_column(void* base, const dm_column_in* in, const dm_column_out* out
   void* xd = (out && out->x_delta) ? nullptr : c.take(d * 4);
   void* xdir = in->main_rows ? c.take((size_t)dm::reencode_dir_words() * 4) : nullptr;
   void* x8 = in->main_rows && dm::reencode_wants_x8(m) ? c.take(m) : nullptr;
+  const uint64_t gdir_n = in->main_rows ? dm::reencode_gdir_entries(m) : 0;
+  void* gdir = gdir_n ? c.take(gdir_n * sizeof(uint2)) : nullptr;
   void* cuts = c.take(((size_t)dm::merge_tiles(m + d, w) + 1) * 8);
   if (cs && base) {
     cs->zero = reinterpret_cast<uint32_t*>(zero);
@@ -73,6 +76,7 @@ size_t carve_column(void* base, const dm_column_in* in, const dm_column_out* out
     cs->slots = static_cast<void**>(slots);
     cs->xdir = static_cast<uint32_t*>(xdir);
     cs->x8 = static_cast<uint8_t*>(x8);
+    cs->gdir = static_cast<uint2*>(gdir);
     dm::Step1Args& a = cs->s1;
     dm::step1_layout(w, m + d, d, cs->zero, &a);
     a.in_keys = in->delta_dict;
@@ -236,6 +240,7 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
   ra.status = ctx->status;
   ra.xdir = cs.xdir;
   ra.x8 = rs.x8 ? cs.x8 : nullptr;
+  ra.gdir = cs.gdir;
   dm::ReencodePlan plan{};
   if (pre_plan) plan = *pre_plan;
   else if (n_out && dm::plan_reencode(in->main_bits, ra, ctx->sm_count, rs.flags, &plan) != cudaSuccess)
@@ -266,6 +271,13 @@ dm_status run_column(dm_ctx* ctx, const dm_column_in* in, const dm_column_out* o
     if (e == cudaSuccess) e = cudaMemsetAsync(out->d_new_bits, 0, sizeof(uint32_t), s);
   }
   if (e != cudaSuccess) return DM_ECUDA;
+  // the global directory (columns past the shared-memory directory's reach)
+  // from the finished X_M
+  e = dm::launch_gdir(plan, ra, s, &ctx->launches);
+  if (e != cudaSuccess) {
+    ctx->last_error = e;
+    return DM_ECUDA;
+  }
   if (timing) {
     cudaEventRecord(ev[1], s);
     cudaEventRecord(ev[2], s);
@@ -500,6 +512,7 @@ bool plan_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, uint32_t fl
     const Resolved rs = resolve(ctx, &in[c], flags, nullptr);
     dm::ReencodeArgs ra = plan_args(&in[c], rs);
     ra.xdir = reinterpret_cast<uint32_t*>(16);   // a directory will exist
+    if (dm::reencode_gdir_entries(in[c].main_dict_len)) ra.gdir = reinterpret_cast<uint2*>(16);
     if (dm::plan_reencode(in[c].main_bits, ra, ctx->sm_count, rs.flags, &(*plans)[c]) != cudaSuccess) return false;
   }
   return true;
@@ -932,6 +945,11 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
   ra.x8 = ra.xdir && dm::reencode_wants_x8(m) && ctx->arena_bytes >= dir_bytes + m
               ? static_cast<uint8_t*>(ctx->arena) + dir_bytes
               : nullptr;
+  // or, past the shared-memory directory's reach, the global directory
+  const size_t gdir_bytes = (size_t)dm::reencode_gdir_entries(m) * sizeof(uint2);
+  ra.gdir = gdir_bytes && n_main && ctx->arena_bytes >= dir_bytes + gdir_bytes
+                ? reinterpret_cast<uint2*>(static_cast<char*>(ctx->arena) + dir_bytes)
+                : nullptr;
   ra.tune_warps = ctx->tuning.reencode_warps;
   ra.tune_stages = ctx->tuning.reencode_stages;
   ra.tune_obufs = ctx->tuning.reencode_obufs;

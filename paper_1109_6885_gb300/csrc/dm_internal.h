@@ -95,6 +95,7 @@ struct ReencodeArgs {
   uint32_t* status;
   uint32_t* xdir;            // scratch for the X_M directory (reencode_dir_words() words) or NULL
   uint8_t* x8;               // scratch for its byte table ([m]) or NULL
+  uint2* gdir;               // scratch for the global directory (reencode_gdir_entries(m)) or NULL
   uint32_t tune_warps;       // 0 = default; warps per block
   uint32_t tune_stages;      // 0 = default; input stages per warp
   uint32_t tune_obufs;       // 0 = default; output buffers per warp
@@ -105,6 +106,9 @@ uint32_t reencode_dir_words();
 uint64_t reencode_dir_max_codes();
 // Whether a column of m main codes gets the directory's byte table.
 bool reencode_wants_x8(uint64_t m);
+// Entries of the global directory of X_M for m main codes (0: m is within
+// the shared-memory directory's reach, which serves it instead).
+uint64_t reencode_gdir_entries(uint64_t m);
 
 // Host-side launch plan of Step 2(b) (opaque storage).
 struct ReencodePlan {
@@ -112,9 +116,12 @@ struct ReencodePlan {
   bool needs_directory;
   uint32_t dir_shift;
   uint32_t dir_entries;
+  uint64_t gdir_entries;     // global directory to build before Step 2(b) (0: none)
 };
 cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, uint32_t flags, ReencodePlan* out);
 cudaError_t launch_xdir(const ReencodePlan& plan, const ReencodeArgs& a, cudaStream_t s, uint64_t* launches);
+// The global directory of the plan, if it has one, built from the finished X_M.
+cudaError_t launch_gdir(const ReencodePlan& plan, const ReencodeArgs& a, cudaStream_t s, uint64_t* launches);
 cudaError_t launch_reencode_planned(const ReencodePlan& plan, const ReencodeArgs& a, cudaStream_t s,
                                     uint64_t* launches);
 cudaError_t launch_reencode(uint32_t b, const ReencodeArgs& a, cudaStream_t stream,

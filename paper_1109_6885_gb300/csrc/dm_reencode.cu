@@ -27,6 +27,7 @@
 // use a plain per-code path.
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "dm_common.cuh"
@@ -51,6 +52,16 @@ constexpr bool RE_X8_B(int b) { return (1ull << b) > RE_X8_MIN_CODES; }
 // kernel fits 64 registers a thread, so two blocks can share an SM.
 constexpr bool RE_DIR_B(int b) { return (1ull << b) > RE_XSMEM_MAX; }
 constexpr int RE_BLOCKS_MIN(int b) { return RE_DIR_B(b) ? 1 : 2; }
+// Input widths whose columns can have more main codes than the shared-memory
+// directory covers; only their kernels carry the global directory lookup.
+constexpr bool RE_GDIR_B(int b) { return (1ull << b) > ((uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX); }
+// The global directory: one 8-byte entry per bucket of 2^s main codes
+// (s >= 6, at most 2M entries, 16 MB, so that it stays in L2): the count c
+// of new values below the bucket's first code, and the offset of the
+// bucket's single step, GDIR_NO_STEP without one, GDIR_MANY with more.
+constexpr uint32_t GDIR_SHIFT_MIN = 6;
+constexpr uint64_t GDIR_MAX_ENTRIES = 1ull << 21;
+constexpr uint32_t GDIR_NO_STEP = 0x7FFFFFFFu, GDIR_MANY = 0xFFFFFFFFu;
 
 template <int B>
 __device__ __forceinline__ void load_row(const uint32_t* row, uint32_t (&w)[B > 0 ? B : 1]) {
@@ -164,9 +175,10 @@ __device__ __forceinline__ uint32_t code_at(const uint32_t* words, uint64_t nwor
 struct Layout {
   uint32_t in_words;    // words of one input stage (32 * b)
   uint32_t out_words;   // words of one output buffer (32 * max_bits)
-  uint32_t x_mode;      // X_M lookup: 0 global gather, 1 direct table in smem, 2 directory in smem
+  uint32_t x_mode;      // X_M lookup: 0 global gather, 1 direct table in smem, 2 directory in smem,
+                        // 3 global directory (L2)
   uint32_t x_entries;   // mode 1: entries of X_M staged; mode 2: directory entries
-  uint32_t dir_shift;   // mode 2: main codes per directory bucket = 2^dir_shift
+  uint32_t dir_shift;   // modes 2, 3: main codes per directory bucket = 2^dir_shift
   uint32_t generic;     // 1: plain per-code path and runtime-width packer on every tile
   uint32_t stages;      // input bulk-copy stages per warp (2..4)
   uint32_t obufs;       // output staging buffers per warp (1..2)
@@ -193,6 +205,34 @@ __global__ void xdir_build_kernel(const uint32_t* __restrict__ xm, uint32_t m, u
   for (uint32_t b = t; b < R; b += nt) dir[b] = xdir_entry<false>(xm, m, s, b, x8 != nullptr);
   if (x8)
     for (uint32_t i = t; i < m; i += nt) x8[i] = xdir_x8<false>(xm, s, i);
+}
+
+// The global directory from the finished X_M: per bucket of 2^s codes the
+// count of new values below it, X_M[lo - 1] - (lo - 1), and its steps,
+// found from X_M at its last code (one, by a binary search, gives the
+// step's offset).
+__global__ void gdir_build_kernel(const uint32_t* __restrict__ xm, uint32_t m, uint32_t s, uint64_t R,
+                                  uint2* __restrict__ gdir) {
+  const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < R; b += nt) {
+    const uint32_t lo = (uint32_t)(b << s);
+    const uint32_t hi = (uint32_t)min((b + 1) << s, (uint64_t)m) - 1;
+    const uint32_t base = lo == 0 ? 0u : __ldg(xm + lo - 1) - (lo - 1);
+    const uint32_t cnt = (__ldg(xm + hi) - hi) - base;
+    uint32_t y = GDIR_NO_STEP;
+    if (cnt == 1) {
+      uint32_t l = lo, h = hi;
+      while (l < h) {
+        const uint32_t mid = l + ((h - l) >> 1);
+        if (__ldg(xm + mid) - mid > base) h = mid;
+        else l = mid + 1;
+      }
+      y = l - lo;
+    } else if (cnt > 1) {
+      y = GDIR_MANY;
+    }
+    gdir[b] = make_uint2(base, y);
+  }
 }
 
 template <int B>
@@ -222,7 +262,7 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32, RE_BLOCKS_MIN(B)) reencode_
   const uint32_t dshift = L.dir_shift, dmask = (1u << L.dir_shift) - 1u;
   const uint64_t stream_policy = policy_evict_first();   // the packed streams pass through once
 
-  if (xmode != 0) {
+  if (xmode == 1 || xmode == 2) {
     const uint32_t* src = xmode == 1 ? a.xm : a.xdir;
     for (uint32_t i = threadIdx.x; i < L.x_entries; i += blockDim.x) s_x[i] = __ldg(src + i);
     __syncthreads();
@@ -313,6 +353,21 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32, RE_BLOCKS_MIN(B)) reencode_
                 x[j] = (e >> 20) == DIR_MANY8_TOP ? c[j] + (e & 0xFFFFFu) + __ldg(a.x8 + c[j]) : __ldg(a.xm + c[j]);
               }
           }
+        }
+      } else if (RE_GDIR_B(B) && xmode == 3) {
+        // the global directory (L2-resident): X_M[c] = c + base + (a step
+        // at or below c's offset); buckets with several steps read X_M
+        uint32_t many = 0;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const uint2 e = __ldg(a.gdir + (c[j] >> dshift));
+          x[j] = c[j] + e.x + ((c[j] & dmask) >= e.y ? 1u : 0u);
+          many |= (e.y == GDIR_MANY ? 1u : 0u) << j;
+        }
+        if (__any_sync(0xFFFFFFFFu, many != 0)) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if ((many >> j) & 1u) x[j] = __ldg(a.xm + c[j]);
         }
       } else if (xmode == 1) {
 #pragma unroll
@@ -488,6 +543,18 @@ uint32_t reencode_dir_words() { return RE_DIR_MAX; }
 uint64_t reencode_dir_max_codes() { return (uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX; }
 bool reencode_wants_x8(uint64_t m) { return m > RE_X8_MIN_CODES && m <= reencode_dir_max_codes(); }
 
+// Bucket shift of the global directory for m main codes.
+static uint32_t gdir_shift(uint64_t m) {
+  uint32_t s = GDIR_SHIFT_MIN;
+  while (((m + (1ull << s) - 1) >> s) > GDIR_MAX_ENTRIES) ++s;
+  return s;
+}
+uint64_t reencode_gdir_entries(uint64_t m) {
+  if (m <= reencode_dir_max_codes()) return 0;
+  const uint32_t s = gdir_shift(m);
+  return (m + (1ull << s) - 1) >> s;
+}
+
 // Host-side launch plan of Step 2(b): lookup mode, block size, shared memory.
 struct ReencodePlanImpl {
   Layout L;
@@ -518,6 +585,9 @@ cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, 
              (uint64_t)a.m <= ((uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX)) {
     L.x_mode = 2;
     xdir_shape(a.m, &L.dir_shift, &L.x_entries);
+  } else if (allow_smem && want_smem && a.gdir && RE_GDIR_B((int)b) && reencode_gdir_entries(a.m)) {
+    L.x_mode = 3;   // nothing in shared memory
+    L.dir_shift = gdir_shift(a.m);
   }
   // warps per block: as many as the device's shared memory allows, up to 16
   // (one block per SM); a lookup table that leaves room for fewer than 4
@@ -534,7 +604,7 @@ cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, 
   };
   const uint32_t want_warps = a.tune_warps >= 1 && a.tune_warps <= RE_WARPS_MAX ? a.tune_warps : 16;
   P.warps = fit(L, want_warps);
-  if (L.x_mode && P.warps < 4) {
+  if ((L.x_mode == 1 || L.x_mode == 2) && P.warps < 4) {
     L.x_mode = 0;
     L.x_entries = 0;
     L.dir_shift = 0;
@@ -565,6 +635,7 @@ cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, 
   out->needs_directory = L.x_mode == 2;
   out->dir_shift = L.dir_shift;
   out->dir_entries = L.x_mode == 2 ? L.x_entries : 0;
+  out->gdir_entries = L.x_mode == 3 ? reencode_gdir_entries(a.m) : 0;
   return cudaSuccess;
 }
 
@@ -576,6 +647,16 @@ cudaError_t launch_xdir(const ReencodePlan& plan, const ReencodeArgs& a, cudaStr
   uint32_t blocks = (work + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   xdir_build_kernel<<<blocks, 256, 0, s>>>(a.xm, a.m, P.L.dir_shift, P.L.x_entries, a.xdir, a.x8);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gdir(const ReencodePlan& plan, const ReencodeArgs& a, cudaStream_t s, uint64_t* launches) {
+  ReencodePlanImpl P;
+  memcpy(&P, plan.storage, sizeof(P));
+  if (P.L.x_mode != 3 || plan.gdir_entries == 0) return cudaSuccess;
+  const uint64_t blocks = std::min<uint64_t>(4096, (plan.gdir_entries + 255) / 256);
+  gdir_build_kernel<<<(uint32_t)blocks, 256, 0, s>>>(a.xm, a.m, P.L.dir_shift, plan.gdir_entries, a.gdir);
   ++*launches;
   return cudaGetLastError();
 }
@@ -596,6 +677,7 @@ cudaError_t launch_reencode(uint32_t b, const ReencodeArgs& a, cudaStream_t s, u
   ReencodePlan plan;
   cudaError_t e = plan_reencode(b, a, sm_count, flags, &plan);
   if (e == cudaSuccess) e = launch_xdir(plan, a, s, launches);
+  if (e == cudaSuccess) e = launch_gdir(plan, a, s, launches);
   if (e == cudaSuccess) e = launch_reencode_planned(plan, a, s, launches);
   return e;
 }

@@ -730,3 +730,84 @@ def test_small_dictionaries_at_and_past_the_one_block_limits(ctx, w, m, d, frac_
     col = column_from_lists(w, um, main_codes, dd, dcodes)
     ref = assert_parity(ctx, col)
     assert ref.u == len(set(um) | set(dd))
+
+
+# ------------------------------------------------------------------ global directory
+# Past 2^24 main codes the shared-memory directory cannot cover X_M; Step 2(b)
+# then reads an L2-resident directory with one 8-byte entry per 64 codes
+# (the count of new values below the bucket and the offset of its single
+# step), and buckets with several steps read X_M.
+
+GDIR_M = (1 << 24) + 300_001          # b = 25, 266,832 buckets of 64 codes
+
+
+def _gdir_column(step_codes, n_random_steps, seed, n_main=1_500_000, above_all=True):
+    """GDIR_M main values 2, 4, 6, ... (8-byte keys).  A new value 2i + 1
+    sorts right below U_M[i], so it puts a step of c = X_M - i at code i:
+    steps at `step_codes` plus `n_random_steps` random codes, one new value
+    above every main value, and as many existing main values again in the
+    delta, in a shuffled insertion order."""
+    rng = np.random.default_rng(seed)
+    m = GDIR_M
+    um = np.arange(m, dtype=np.uint64) * 2 + 2
+    steps = np.unique(np.concatenate([np.array(step_codes, np.uint64),
+                                      rng.integers(0, m, n_random_steps).astype(np.uint64)]))
+    new = steps * 2 + 1
+    if above_all:
+        new = np.append(new, np.uint64(2 * m + 9))
+    old = um[rng.integers(0, m, new.size)]
+    dd = np.concatenate([new, old, new[: new.size // 4]])      # repeats inside D_dict too
+    dd = dd[rng.permutation(dd.size)]
+    mc = rng.integers(0, m, n_main).astype(np.uint32)
+    b = synth.bits_for(m)
+    dc = rng.integers(0, dd.size, 20_000).astype(np.uint32)
+    spec = synth.ColumnSpec(n_main=n_main, m=m, w=8, n_delta=dc.size)
+    return synth.Column(spec, um, mc, b, synth.pack(mc, b), np.ascontiguousarray(dd), dc)
+
+
+def test_global_directory_steps_at_bucket_edges(ctx):
+    # bucket 0: a step at code 0 only; bucket 1: offset 0 (code 64);
+    # bucket 2: offset 63 (code 191); bucket 3: two steps; bucket 5: ten;
+    # the last main code; a bucket whose first and last codes both step
+    edge = [0, 64, 191, 200, 210] + list(range(320, 330)) + [GDIR_M - 1, 640, 703]
+    col = _gdir_column(edge, 2_000, seed=31)
+    ref = assert_parity(ctx, col)
+    new_values = np.unique(col.delta_dict[col.delta_dict % 2 == 1]).size
+    assert ref.u == GDIR_M + new_values
+    # the plain X_M gather gives the same bytes
+    assert_parity(ctx, col, dm.DM_FLAG_X_GLOBAL, ref)
+
+
+@pytest.mark.parametrize("n_steps", [0, 150_000, 3_000_000])
+def test_global_directory_step_densities(ctx, n_steps):
+    """No new value below any main value (every bucket without a step), a
+    sparse mix (mostly single-step buckets) and a dense one (almost every
+    bucket crowded, read through X_M)."""
+    col = _gdir_column([], n_steps, seed=40 + n_steps % 97, above_all=True)
+    assert_parity(ctx, col)
+
+
+def test_global_directory_flags_codes_past_the_dictionary(ctx):
+    """Codes >= |U_M| at b = 25 are flagged and clamped, never faulting, on
+    the standalone Step 2(b) entry point, which builds the global directory
+    itself."""
+    import torch
+    rng = np.random.default_rng(78)
+    m = GDIR_M
+    c = np.zeros(m, np.uint32)
+    c[rng.integers(0, m, 40_000)] = 1
+    xm = (np.arange(m, dtype=np.uint64) + np.cumsum(c)).astype(np.uint32)     # X_M with steps
+    b = synth.bits_for(m)
+    bo = synth.bits_for(int(xm[-1]) + 1)
+    mc = rng.integers(0, m, 1_100_000).astype(np.uint32)
+    mc[::1000] = rng.integers(m, 2**b, mc[::1000].size)       # invalid codes
+    main = synth.pack(mc, b)
+    out = torch.zeros(dm.dm_packed_bytes(mc.size, bo) // 4, dtype=torch.int32, device="cuda")
+    bits = torch.tensor([bo], dtype=torch.int32, device="cuda")
+    dm.dm_reencode(ctx, dm.to_device(main), b, mc.size, None, 0, dm.to_device(xm), m, None, 0, bits,
+                   bo, out, None, 0)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_ECODE
+    got = np.array(_brute.unpack_bits(dm.to_host(out, np.uint32)[:20_000], 10_000, bo))
+    want = xm[np.minimum(mc[:10_000], m - 1)]
+    assert np.array_equal(got, want)
