@@ -116,8 +116,8 @@ struct MergeSmem {
   // [0, na): per U_M entry, the U_D entries placed right before it, then
   // their prefix; [na, na + nb): the U_D segment's insertion codes
   alignas(16) uint32_t ap[T];
-  uint32_t rank[T];                // per U_D entry: U_M entries of the tile at or below it
-  uint32_t ndx[T + 1];             // per U_D entry: non-duplicate U_D entries before it (and the total)
+  uint16_t rank[T];                // per U_D entry: U_M entries of the tile at or below it
+  uint16_t ndx[T + 1];             // per U_D entry: non-duplicate U_D entries before it (and the total)
   uint32_t wsum[S1_WARPS];
   uint64_t cut[2];
   uint64_t excl, lb_sum;
@@ -125,6 +125,16 @@ struct MergeSmem {
   uint32_t next_tile;
   K prevA, prevB;
 };
+
+static_assert(mg_tile(4) < 65536 && mg_tile(16) < 65536, "16-bit ranks within a tile");
+
+// Shared memory of the split form's merge kernel (the merge phase alone),
+// and its blocks per SM: three with 4- and 8-byte keys, two with 16-byte.
+template <int W>
+constexpr size_t merge_smem_bytes() {
+  return (sizeof(MergeSmem<W>) + 15) / 16 * 16;
+}
+constexpr int merge_blocks_min(int w) { return w == 16 ? 2 : 3; }
 
 constexpr uint32_t BK_CAP = 2048;     // keys a block sorts in shared memory at once
 constexpr uint32_t BK_SINGLE = BK_CAP;  // at most this many keys: one block sorts them all
@@ -1315,7 +1325,7 @@ __global__ void __launch_bounds__(S1_THREADS) step1_cut_kernel(Step1Args a) {
 
 // The merge tiles, each block taking the next from a counter.
 template <int W>
-__global__ void __launch_bounds__(S1_THREADS, 2) step1_merge_kernel(Step1Args a) {
+__global__ void __launch_bounds__(S1_THREADS, merge_blocks_min(W)) step1_merge_kernel(Step1Args a) {
   using K = typename KeyOf<W>::T;
   extern __shared__ __align__(16) unsigned char dsmem[];
   Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
@@ -1360,6 +1370,7 @@ struct Launch {
   std::mutex mu;
   bool ready[kLaunchDevices][3] = {};
   int per_sm[kLaunchDevices][3] = {};
+  int merge_per_sm[kLaunchDevices][3] = {};   // step1_merge_kernel<W>
 };
 Launch& launch_state() {
   static Launch L;
@@ -1385,10 +1396,16 @@ int prepare_w(cudaError_t* err) {
   if (L.ready[dev][wi]) return L.per_sm[dev][wi];
   const size_t smem = step1_smem_bytes<W>();
   cudaError_t e = cudaFuncSetAttribute(step1_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  for (const void* fn : {(const void*)step1_merge_kernel<W>, (const void*)step1_hist_kernel<W>,
-                         (const void*)step1_pass_kernel<W>, (const void*)step1_msd_kernel<W>,
-                         (const void*)step1_bucket_kernel<W>})
+  for (const void* fn : {(const void*)step1_hist_kernel<W>, (const void*)step1_pass_kernel<W>,
+                         (const void*)step1_msd_kernel<W>, (const void*)step1_bucket_kernel<W>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step1_merge_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)merge_smem_bytes<W>());
+  int merge_per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&merge_per_sm, step1_merge_kernel<W>, S1_THREADS,
+                                                      merge_smem_bytes<W>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(step1_small_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)small_smem_bytes<W>());
@@ -1397,6 +1414,7 @@ int prepare_w(cudaError_t* err) {
   *err = e;
   if (e != cudaSuccess) return 0;
   L.per_sm[dev][wi] = per_sm;
+  L.merge_per_sm[dev][wi] = merge_per_sm > 0 ? merge_per_sm : 1;
   L.ready[dev][wi] = true;
   return per_sm;
 }
@@ -1426,8 +1444,13 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
   // which finds the sorted keys where the sort left them)
   const bool capped = cap < full && a.final_slot != nullptr;
   const bool split_sort = capped && (a.phases & S1_SORT) && a.d > BK_SINGLE && a.sort_tiles > 4 * cap;
-  const bool split = capped && (a.phases & S1_MERGE) && a.m + a.d > 0 && a.cuts != nullptr &&
-                     (a.merge_tiles > cap || split_sort);
+  // a merge of more tiles than the cooperative grid holds at once also
+  // takes the split form, uncapped: its merge kernel's blocks need no
+  // co-residency and fit more to an SM (16-bit per-tile arrays, fewer
+  // registers), so more latency-bound tiles are in flight
+  const bool multiwave = a.final_slot != nullptr && a.merge_tiles > full;
+  const bool split = (a.phases & S1_MERGE) && a.m + a.d > 0 && a.cuts != nullptr &&
+                     ((capped && (a.merge_tiles > cap || split_sort)) || multiwave);
   Step1Args c = a;
   if (split) c.phases &= S1_SORT;
   if (split_sort) c.phases = 0;
@@ -1475,7 +1498,11 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
   const uint32_t cut_blocks = (uint32_t)std::min<uint64_t>(full, (a.merge_tiles + S1_WARPS) / S1_WARPS);
   step1_cut_kernel<W><<<cut_blocks, S1_THREADS, 0, s>>>(a);
   ++*launches;
-  step1_merge_kernel<W><<<(uint32_t)std::min<uint64_t>(full, a.merge_tiles), S1_THREADS, smem, s>>>(a);
+  int dev = 0;
+  if (current_device(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+  const uint64_t merge_full = (uint64_t)launch_state().merge_per_sm[dev][W == 4 ? 0 : (W == 8 ? 1 : 2)] * sm_count;
+  step1_merge_kernel<W><<<(uint32_t)std::min<uint64_t>(std::max<uint64_t>(merge_full, 1), a.merge_tiles),
+                          S1_THREADS, merge_smem_bytes<W>(), s>>>(a);
   ++*launches;
   if ((a.phases & S1_DIR) && a.dir_entries > 0) {
     const uint64_t work = std::max<uint64_t>(a.dir_entries, a.x8 ? a.m : 0);
