@@ -67,7 +67,7 @@ size_t carve_column(void* base, const dm_column_in* in, const dm_column_out* out
   void* xd = (out && out->x_delta) ? nullptr : c.take(d * 4);
   void* xdir = in->main_rows ? c.take((size_t)dm::reencode_dir_words() * 4) : nullptr;
   void* x8 = in->main_rows && dm::reencode_wants_x8(m) ? c.take(m) : nullptr;
-  const uint64_t gdir_n = in->main_rows ? dm::reencode_gdir_entries(m) : 0;
+  const uint64_t gdir_n = in->main_rows ? dm::reencode_gdir_entries(m, d) : 0;
   void* gdir = gdir_n ? c.take(gdir_n * sizeof(uint2)) : nullptr;
   void* cuts = c.take(((size_t)dm::merge_tiles(m + d, w) + 1) * 8);
   if (cs && base) {
@@ -204,6 +204,7 @@ dm::ReencodeArgs plan_args(const dm_column_in* in, const Resolved& r) {
   ra.n_main = in->main_rows;
   ra.n_delta = in->delta_rows;
   ra.m = (uint32_t)std::min<uint64_t>(in->main_dict_len, 0xFFFFFFFFu);
+  ra.d = (uint32_t)std::min<uint64_t>(in->delta_dict_len, 0xFFFFFFFFu);
   ra.max_bits = bits_for(in->main_dict_len + in->delta_dict_len);
   ra.tune_warps = r.warps;
   ra.tune_stages = r.stages;
@@ -512,7 +513,7 @@ bool plan_table(dm_ctx* ctx, const dm_column_in* in, uint32_t ncols, uint32_t fl
     const Resolved rs = resolve(ctx, &in[c], flags, nullptr);
     dm::ReencodeArgs ra = plan_args(&in[c], rs);
     ra.xdir = reinterpret_cast<uint32_t*>(16);   // a directory will exist
-    if (dm::reencode_gdir_entries(in[c].main_dict_len)) ra.gdir = reinterpret_cast<uint2*>(16);
+    if (dm::reencode_gdir_entries(in[c].main_dict_len, in[c].delta_dict_len)) ra.gdir = reinterpret_cast<uint2*>(16);
     if (dm::plan_reencode(in[c].main_bits, ra, ctx->sm_count, rs.flags, &(*plans)[c]) != cudaSuccess) return false;
   }
   return true;
@@ -946,7 +947,7 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
               ? static_cast<uint8_t*>(ctx->arena) + dir_bytes
               : nullptr;
   // or, past the shared-memory directory's reach, the global directory
-  const size_t gdir_bytes = (size_t)dm::reencode_gdir_entries(m) * sizeof(uint2);
+  const size_t gdir_bytes = (size_t)dm::reencode_gdir_entries(m, d) * sizeof(uint2);
   ra.gdir = gdir_bytes && n_main && ctx->arena_bytes >= dir_bytes + gdir_bytes
                 ? reinterpret_cast<uint2*>(static_cast<char*>(ctx->arena) + dir_bytes)
                 : nullptr;

@@ -95,7 +95,7 @@ struct ReencodeArgs {
   uint32_t* status;
   uint32_t* xdir;            // scratch for the X_M directory (reencode_dir_words() words) or NULL
   uint8_t* x8;               // scratch for its byte table ([m]) or NULL
-  uint2* gdir;               // scratch for the global directory (reencode_gdir_entries(m)) or NULL
+  uint2* gdir;               // scratch for the global directory (reencode_gdir_entries(m, d)) or NULL
   uint32_t tune_warps;       // 0 = default; warps per block
   uint32_t tune_stages;      // 0 = default; input stages per warp
   uint32_t tune_obufs;       // 0 = default; output buffers per warp
@@ -106,9 +106,10 @@ uint32_t reencode_dir_words();
 uint64_t reencode_dir_max_codes();
 // Whether a column of m main codes gets the directory's byte table.
 bool reencode_wants_x8(uint64_t m);
-// Entries of the global directory of X_M for m main codes (0: m is within
-// the shared-memory directory's reach, which serves it instead).
-uint64_t reencode_gdir_entries(uint64_t m);
+// Entries of the global directory of X_M for m main codes and d delta
+// dictionary entries (0: none; m is within the shared-memory directory's
+// reach, which serves it instead, or too large for one).
+uint64_t reencode_gdir_entries(uint64_t m, uint64_t d);
 
 // Host-side launch plan of Step 2(b) (opaque storage).
 struct ReencodePlan {

@@ -56,12 +56,17 @@ constexpr int RE_BLOCKS_MIN(int b) { return RE_DIR_B(b) ? 1 : 2; }
 // directory covers; only their kernels carry the global directory lookup.
 constexpr bool RE_GDIR_B(int b) { return (1ull << b) > ((uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX); }
 // The global directory: one 8-byte entry per bucket of 2^s main codes
-// (s >= 6, at most 2M entries, 16 MB, so that it stays in L2): the count c
-// of new values below the bucket's first code, and the offset of the
-// bucket's single step, GDIR_NO_STEP without one, GDIR_MANY with more.
-constexpr uint32_t GDIR_SHIFT_MIN = 6;
-constexpr uint64_t GDIR_MAX_ENTRIES = 1ull << 21;
-constexpr uint32_t GDIR_NO_STEP = 0x7FFFFFFFu, GDIR_MANY = 0xFFFFFFFFu;
+// (3 <= s <= 6, at most 4M entries, 32 MB, so that it stays in L2): the
+// count c of new values below the bucket's first code, and the offsets in
+// the bucket of its first four steps, one byte each in increasing order,
+// GDIR_UNUSED past the last; GDIR_MANY marks a bucket of more than four.
+// A step is a code where c grows; a code where it grows by two holds two.
+// s is picked from |U_M| / |D_dict| (|D_dict| bounds the new values) for
+// about 1.5 steps a bucket at most, so that few buckets are crowded.
+constexpr uint32_t GDIR_SHIFT_MIN = 3, GDIR_SHIFT_MAX = 6;
+constexpr uint64_t GDIR_MAX_ENTRIES = 1ull << 22;
+constexpr uint32_t GDIR_UNUSED = 0x7Fu, GDIR_MANY = 0xFFFFFFFFu;
+static_assert((1u << GDIR_SHIFT_MAX) <= GDIR_UNUSED, "offsets below the unused mark");
 
 template <int B>
 __device__ __forceinline__ void load_row(const uint32_t* row, uint32_t (&w)[B > 0 ? B : 1]) {
@@ -208,9 +213,9 @@ __global__ void xdir_build_kernel(const uint32_t* __restrict__ xm, uint32_t m, u
 }
 
 // The global directory from the finished X_M: per bucket of 2^s codes the
-// count of new values below it, X_M[lo - 1] - (lo - 1), and its steps,
-// found from X_M at its last code (one, by a binary search, gives the
-// step's offset).
+// count of new values below it, X_M[lo - 1] - (lo - 1), and the steps in
+// it, X_M at its last code less that; with at most four, the k-th step's
+// offset is the first code whose count reaches base + k (a binary search).
 __global__ void gdir_build_kernel(const uint32_t* __restrict__ xm, uint32_t m, uint32_t s, uint64_t R,
                                   uint2* __restrict__ gdir) {
   const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
@@ -219,19 +224,22 @@ __global__ void gdir_build_kernel(const uint32_t* __restrict__ xm, uint32_t m, u
     const uint32_t hi = (uint32_t)min((b + 1) << s, (uint64_t)m) - 1;
     const uint32_t base = lo == 0 ? 0u : __ldg(xm + lo - 1) - (lo - 1);
     const uint32_t cnt = (__ldg(xm + hi) - hi) - base;
-    uint32_t y = GDIR_NO_STEP;
-    if (cnt == 1) {
-      uint32_t l = lo, h = hi;
-      while (l < h) {
-        const uint32_t mid = l + ((h - l) >> 1);
-        if (__ldg(xm + mid) - mid > base) h = mid;
-        else l = mid + 1;
+    uint32_t offs = GDIR_UNUSED * 0x01010101u;
+    if (cnt > 4) {
+      offs = GDIR_MANY;
+    } else {
+      for (uint32_t k = 1; k <= cnt; ++k) {
+        uint32_t l = lo, h = hi;
+        while (l < h) {
+          const uint32_t mid = l + ((h - l) >> 1);
+          if (__ldg(xm + mid) - mid >= base + k) h = mid;
+          else l = mid + 1;
+        }
+        const uint32_t sh = 8 * (k - 1);
+        offs = (offs & ~(0xFFu << sh)) | ((l - lo) << sh);
       }
-      y = l - lo;
-    } else if (cnt > 1) {
-      y = GDIR_MANY;
     }
-    gdir[b] = make_uint2(base, y);
+    gdir[b] = make_uint2(offs, base);
   }
 }
 
@@ -355,14 +363,18 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32, RE_BLOCKS_MIN(B)) reencode_
           }
         }
       } else if (RE_GDIR_B(B) && xmode == 3) {
-        // the global directory (L2-resident): X_M[c] = c + base + (a step
-        // at or below c's offset); buckets with several steps read X_M
+        // the global directory (L2-resident): X_M[c] = c + base + (steps at
+        // or below c's offset); buckets with more than four read X_M
+        // steps at or below the code's offset lo: a byte k of the offsets
+        // word counts when (lo + 128) - offset_k keeps its top bit, byte by
+        // byte without borrows (offsets and lo below 128)
         uint32_t many = 0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const uint2 e = __ldg(a.gdir + (c[j] >> dshift));
-          x[j] = c[j] + e.x + ((c[j] & dmask) >= e.y ? 1u : 0u);
-          many |= (e.y == GDIR_MANY ? 1u : 0u) << j;
+          const uint32_t lo4 = ((c[j] & dmask) * 0x01010101u) | 0x80808080u;
+          x[j] = c[j] + e.y + __popc((lo4 - e.x) & 0x80808080u);
+          many |= (e.x == GDIR_MANY ? 1u : 0u) << j;
         }
         if (__any_sync(0xFFFFFFFFu, many != 0)) {
 #pragma unroll
@@ -543,16 +555,18 @@ uint32_t reencode_dir_words() { return RE_DIR_MAX; }
 uint64_t reencode_dir_max_codes() { return (uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX; }
 bool reencode_wants_x8(uint64_t m) { return m > RE_X8_MIN_CODES && m <= reencode_dir_max_codes(); }
 
-// Bucket shift of the global directory for m main codes.
-static uint32_t gdir_shift(uint64_t m) {
-  uint32_t s = GDIR_SHIFT_MIN;
-  while (((m + (1ull << s) - 1) >> s) > GDIR_MAX_ENTRIES) ++s;
-  return s;
-}
-uint64_t reencode_gdir_entries(uint64_t m) {
+// Bucket shift of the global directory for m main codes and d delta values
+// (0: no global directory).
+static uint32_t gdir_shift(uint64_t m, uint64_t d) {
   if (m <= reencode_dir_max_codes()) return 0;
-  const uint32_t s = gdir_shift(m);
-  return (m + (1ull << s) - 1) >> s;
+  uint32_t s = GDIR_SHIFT_MAX;
+  while (s > GDIR_SHIFT_MIN && 2 * (d << s) > 3 * m) --s;
+  while (((m + (1ull << s) - 1) >> s) > GDIR_MAX_ENTRIES) ++s;
+  return s <= GDIR_SHIFT_MAX ? s : 0;
+}
+uint64_t reencode_gdir_entries(uint64_t m, uint64_t d) {
+  const uint32_t s = gdir_shift(m, d);
+  return s ? (m + (1ull << s) - 1) >> s : 0;
 }
 
 // Host-side launch plan of Step 2(b): lookup mode, block size, shared memory.
@@ -585,9 +599,9 @@ cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, 
              (uint64_t)a.m <= ((uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX)) {
     L.x_mode = 2;
     xdir_shape(a.m, &L.dir_shift, &L.x_entries);
-  } else if (allow_smem && want_smem && a.gdir && RE_GDIR_B((int)b) && reencode_gdir_entries(a.m)) {
+  } else if (allow_smem && want_smem && a.gdir && RE_GDIR_B((int)b) && reencode_gdir_entries(a.m, a.d)) {
     L.x_mode = 3;   // nothing in shared memory
-    L.dir_shift = gdir_shift(a.m);
+    L.dir_shift = gdir_shift(a.m, a.d);
   }
   // warps per block: as many as the device's shared memory allows, up to 16
   // (one block per SM); a lookup table that leaves room for fewer than 4
@@ -635,7 +649,7 @@ cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, 
   out->needs_directory = L.x_mode == 2;
   out->dir_shift = L.dir_shift;
   out->dir_entries = L.x_mode == 2 ? L.x_entries : 0;
-  out->gdir_entries = L.x_mode == 3 ? reencode_gdir_entries(a.m) : 0;
+  out->gdir_entries = L.x_mode == 3 ? reencode_gdir_entries(a.m, a.d) : 0;
   return cudaSuccess;
 }
 

@@ -734,27 +734,29 @@ def test_small_dictionaries_at_and_past_the_one_block_limits(ctx, w, m, d, frac_
 
 # ------------------------------------------------------------------ global directory
 # Past 2^24 main codes the shared-memory directory cannot cover X_M; Step 2(b)
-# then reads an L2-resident directory with one 8-byte entry per 64 codes
-# (the count of new values below the bucket and the offset of its single
-# step), and buckets with several steps read X_M.
+# then reads an L2-resident directory with one 8-byte entry per bucket of
+# 2^s codes (the count of new values below the bucket and the offsets of up
+# to four steps), and buckets with more steps read X_M.
 
-GDIR_M = (1 << 24) + 300_001          # b = 25, 266,832 buckets of 64 codes
+GDIR_M = (1 << 24) + 300_001          # b = 25
 
 
-def _gdir_column(step_codes, n_random_steps, seed, n_main=1_500_000, above_all=True):
-    """GDIR_M main values 2, 4, 6, ... (8-byte keys).  A new value 2i + 1
-    sorts right below U_M[i], so it puts a step of c = X_M - i at code i:
-    steps at `step_codes` plus `n_random_steps` random codes, one new value
-    above every main value, and as many existing main values again in the
-    delta, in a shuffled insertion order."""
+def _gdir_column(steps, n_random_steps, seed, n_main=1_500_000, above_all=True):
+    """GDIR_M main values 4, 8, 12, ... (8-byte keys).  New values 4i + 1,
+    4i + 2, 4i + 3 sort right below U_M[i], so k of them put a step of k at
+    code i (c = X_M - i grows by k there): `steps` is a list of (code, k),
+    plus `n_random_steps` single steps at random codes, one new value above
+    every main value, and as many existing main values again in the delta,
+    in a shuffled insertion order."""
     rng = np.random.default_rng(seed)
     m = GDIR_M
-    um = np.arange(m, dtype=np.uint64) * 2 + 2
-    steps = np.unique(np.concatenate([np.array(step_codes, np.uint64),
-                                      rng.integers(0, m, n_random_steps).astype(np.uint64)]))
-    new = steps * 2 + 1
+    um = np.arange(m, dtype=np.uint64) * 4 + 4
+    new = [np.uint64(4 * i + j) for i, k in steps for j in range(1, k + 1)]
+    rand = np.setdiff1d(rng.integers(0, m, n_random_steps).astype(np.uint64),
+                        np.array([i for i, _ in steps], np.uint64))
+    new = np.concatenate([np.array(new, np.uint64), rand * 4 + 1])
     if above_all:
-        new = np.append(new, np.uint64(2 * m + 9))
+        new = np.append(new, np.uint64(4 * m + 9))
     old = um[rng.integers(0, m, new.size)]
     dd = np.concatenate([new, old, new[: new.size // 4]])      # repeats inside D_dict too
     dd = dd[rng.permutation(dd.size)]
@@ -766,13 +768,18 @@ def _gdir_column(step_codes, n_random_steps, seed, n_main=1_500_000, above_all=T
 
 
 def test_global_directory_steps_at_bucket_edges(ctx):
-    # bucket 0: a step at code 0 only; bucket 1: offset 0 (code 64);
-    # bucket 2: offset 63 (code 191); bucket 3: two steps; bucket 5: ten;
-    # the last main code; a bucket whose first and last codes both step
-    edge = [0, 64, 191, 200, 210] + list(range(320, 330)) + [GDIR_M - 1, 640, 703]
-    col = _gdir_column(edge, 2_000, seed=31)
+    """With a small delta the buckets are 64 codes: a step at code 0; one at
+    offset 0 and one at offset 63 of their buckets; two; exactly four; five
+    (more than an entry holds); three at one code; two double steps; a
+    triple and a double (five); the last main code; the first and last
+    codes of one bucket."""
+    M = GDIR_M
+    steps = [(0, 1), (64, 1), (191, 1), (200, 1), (210, 1), (256, 1), (260, 1), (300, 1), (319, 1),
+             (320, 1), (321, 1), (322, 1), (330, 1), (383, 1), (400, 3), (448, 2), (460, 2), (512, 3),
+             (513, 2), (640, 1), (703, 1), (M - 1, 1)]
+    col = _gdir_column(steps, 2_000, seed=31)
     ref = assert_parity(ctx, col)
-    new_values = np.unique(col.delta_dict[col.delta_dict % 2 == 1]).size
+    new_values = np.unique(col.delta_dict[col.delta_dict % 4 != 0]).size
     assert ref.u == GDIR_M + new_values
     # the plain X_M gather gives the same bytes
     assert_parity(ctx, col, dm.DM_FLAG_X_GLOBAL, ref)
@@ -780,9 +787,9 @@ def test_global_directory_steps_at_bucket_edges(ctx):
 
 @pytest.mark.parametrize("n_steps", [0, 150_000, 3_000_000])
 def test_global_directory_step_densities(ctx, n_steps):
-    """No new value below any main value (every bucket without a step), a
-    sparse mix (mostly single-step buckets) and a dense one (almost every
-    bucket crowded, read through X_M)."""
+    """No new value below any main value (no bucket with a step), a sparse
+    mix, and a dense one (3M steps among 17M codes: the delta's size makes
+    the buckets 8 codes, a few of them crowded)."""
     col = _gdir_column([], n_steps, seed=40 + n_steps % 97, above_all=True)
     assert_parity(ctx, col)
 
