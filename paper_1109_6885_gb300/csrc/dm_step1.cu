@@ -175,6 +175,13 @@ template <int W>
 constexpr size_t step1_smem_bytes() {
   return (sizeof(Step1Smem<W>) + 15) / 16 * 16 + 64;
 }
+// The split form's histogram, pass and partition kernels: the sort phase's
+// memory (the plan and one sort tile) and the scan's warp sums after it.
+template <int W>
+constexpr size_t sort_smem_bytes() {
+  return (sizeof(SortPhase<W>) + 15) / 16 * 16 + 64;
+}
+constexpr int SORT_BLOCKS_MIN = 3;
 
 // ---------------------------------------------------------------- Step 1(a)
 // Digit counts of every pass (blocks below hist_blocks take part; each
@@ -1225,41 +1232,40 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
 // byte instead (and the reverse), return at once.
 
 template <int W>
-__global__ void __launch_bounds__(S1_THREADS, 2) step1_hist_kernel(Step1Args a) {
+__global__ void __launch_bounds__(S1_THREADS, SORT_BLOCKS_MIN) step1_hist_kernel(Step1Args a) {
   extern __shared__ __align__(16) unsigned char dsmem[];
-  Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
-  hist_phase<W>(a, U.hist);
+  hist_phase<W>(a, reinterpret_cast<uint32_t*>(dsmem));   // W * 256 counters
 }
 
 template <int W>
-__global__ void __launch_bounds__(S1_THREADS, 2) step1_pass_kernel(Step1Args a, int pass) {
+__global__ void __launch_bounds__(S1_THREADS, SORT_BLOCKS_MIN) step1_pass_kernel(Step1Args a, int pass) {
   extern __shared__ __align__(16) unsigned char dsmem[];
-  Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
-  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(Step1Smem<W>) + 15) / 16 * 16);
+  SortPhase<W>& SP = *reinterpret_cast<SortPhase<W>*>(dsmem);
+  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(SortPhase<W>) + 15) / 16 * 16);
   bool msd = false;
-  const uint32_t run = plan_phase<W>(a, U.sp.plan, s_wsum, &msd);
+  const uint32_t run = plan_phase<W>(a, SP.plan, s_wsum, &msd);
   if (msd || !((run >> pass) & 1u)) return;
   const int e = __popc(run & ((1u << pass) - 1u));
   for (;;) {
-    if (threadIdx.x == 0) U.sp.s.next = atomicAdd(a.barriers + pass, 1u);
+    if (threadIdx.x == 0) SP.s.next = atomicAdd(a.barriers + pass, 1u);
     __syncthreads();
-    const uint32_t t = U.sp.s.next;
+    const uint32_t t = SP.s.next;
     __syncthreads();
     if (t >= a.sort_tiles) break;
-    pass_tile<W>(a, pass, t, e, U.sp.plan, U.sp.s);
+    pass_tile<W>(a, pass, t, e, SP.plan, SP.s);
   }
 }
 
 template <int W>
-__global__ void __launch_bounds__(S1_THREADS, 2) step1_msd_kernel(Step1Args a) {
+__global__ void __launch_bounds__(S1_THREADS, SORT_BLOCKS_MIN) step1_msd_kernel(Step1Args a) {
   extern __shared__ __align__(16) unsigned char dsmem[];
-  Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
-  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(Step1Smem<W>) + 15) / 16 * 16);
+  SortPhase<W>& SP = *reinterpret_cast<SortPhase<W>*>(dsmem);
+  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(SortPhase<W>) + 15) / 16 * 16);
   bool msd = false;
-  const uint32_t run = plan_phase<W>(a, U.sp.plan, s_wsum, &msd);
+  const uint32_t run = plan_phase<W>(a, SP.plan, s_wsum, &msd);
   if (!msd) return;
   const int top = 31 - __clz(run);
-  for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) msd_tile<W>(a, top, t, U.sp.plan, U.sp.s);
+  for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) msd_tile<W>(a, top, t, SP.plan, SP.s);
 }
 
 // The buckets of the top-byte partition, each sorted in shared memory; and
@@ -1371,6 +1377,7 @@ struct Launch {
   bool ready[kLaunchDevices][3] = {};
   int per_sm[kLaunchDevices][3] = {};
   int merge_per_sm[kLaunchDevices][3] = {};   // step1_merge_kernel<W>
+  int sort_per_sm[kLaunchDevices][3] = {};    // step1_hist / pass / msd_kernel<W>
 };
 Launch& launch_state() {
   static Launch L;
@@ -1396,9 +1403,16 @@ int prepare_w(cudaError_t* err) {
   if (L.ready[dev][wi]) return L.per_sm[dev][wi];
   const size_t smem = step1_smem_bytes<W>();
   cudaError_t e = cudaFuncSetAttribute(step1_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step1_bucket_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (const void* fn : {(const void*)step1_hist_kernel<W>, (const void*)step1_pass_kernel<W>,
-                         (const void*)step1_msd_kernel<W>, (const void*)step1_bucket_kernel<W>})
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                         (const void*)step1_msd_kernel<W>})
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem_bytes<W>());
+  int sort_per_sm = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sort_per_sm, step1_pass_kernel<W>, S1_THREADS,
+                                                      sort_smem_bytes<W>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(step1_merge_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)merge_smem_bytes<W>());
@@ -1415,6 +1429,7 @@ int prepare_w(cudaError_t* err) {
   if (e != cudaSuccess) return 0;
   L.per_sm[dev][wi] = per_sm;
   L.merge_per_sm[dev][wi] = merge_per_sm > 0 ? merge_per_sm : 1;
+  L.sort_per_sm[dev][wi] = sort_per_sm > 0 ? sort_per_sm : 1;
   L.ready[dev][wi] = true;
   return per_sm;
 }
@@ -1443,14 +1458,19 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
   // quarter of the sort's: the split form (a split sort implies a split merge,
   // which finds the sorted keys where the sort left them)
   const bool capped = cap < full && a.final_slot != nullptr;
-  const bool split_sort = capped && (a.phases & S1_SORT) && a.d > BK_SINGLE && a.sort_tiles > 4 * cap;
+  // a sort of more than four times as many tiles as the grid holds at once
+  // takes the split form too, whose histogram, pass and partition kernels
+  // fit three blocks to an SM (below that the split form's extra launches
+  // cost more than they save)
+  const bool split_sort = a.final_slot != nullptr && (a.phases & S1_SORT) && a.d > BK_SINGLE &&
+                          ((capped && a.sort_tiles > 4 * cap) || a.sort_tiles > 4 * full);
   // a merge of more tiles than the cooperative grid holds at once also
   // takes the split form, uncapped: its merge kernel's blocks need no
   // co-residency and fit more to an SM (16-bit per-tile arrays, fewer
   // registers), so more latency-bound tiles are in flight
   const bool multiwave = a.final_slot != nullptr && a.merge_tiles > full;
   const bool split = (a.phases & S1_MERGE) && a.m + a.d > 0 && a.cuts != nullptr &&
-                     ((capped && (a.merge_tiles > cap || split_sort)) || multiwave);
+                     ((capped && a.merge_tiles > cap) || multiwave || split_sort);
   Step1Args c = a;
   if (split) c.phases &= S1_SORT;
   if (split_sort) c.phases = 0;
@@ -1480,17 +1500,23 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
     ++*launches;
   }
   if (e != cudaSuccess) return e;
+  int dev = 0;
+  if (current_device(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+  const int wi = W == 4 ? 0 : (W == 8 ? 1 : 2);
   if (split_sort) {
+    const uint64_t sort_full = std::max<uint64_t>(1, (uint64_t)launch_state().sort_per_sm[dev][wi] * sm_count);
+    const size_t ssm = sort_smem_bytes<W>();
     Step1Args h = a;
-    h.hist_blocks = (uint32_t)std::min<uint64_t>(full, (a.d + S1_THREADS * HI_ITEMS - 1) / (S1_THREADS * HI_ITEMS));
-    step1_hist_kernel<W><<<h.hist_blocks, S1_THREADS, smem, s>>>(h);
+    h.hist_blocks =
+        (uint32_t)std::min<uint64_t>(sort_full, (a.d + S1_THREADS * HI_ITEMS - 1) / (S1_THREADS * HI_ITEMS));
+    step1_hist_kernel<W><<<h.hist_blocks, S1_THREADS, ssm, s>>>(h);
     ++*launches;
-    const uint32_t sort_grid = (uint32_t)std::min<uint64_t>(full, a.sort_tiles);
+    const uint32_t sort_grid = (uint32_t)std::min<uint64_t>(sort_full, a.sort_tiles);
     for (int p = 0; p < W; ++p) {
-      step1_pass_kernel<W><<<sort_grid, S1_THREADS, smem, s>>>(a, p);
+      step1_pass_kernel<W><<<sort_grid, S1_THREADS, ssm, s>>>(a, p);
       ++*launches;
     }
-    step1_msd_kernel<W><<<sort_grid, S1_THREADS, smem, s>>>(a);
+    step1_msd_kernel<W><<<sort_grid, S1_THREADS, ssm, s>>>(a);
     step1_bucket_kernel<W><<<(uint32_t)std::min<uint64_t>(full, 256), S1_THREADS, smem, s>>>(a);
     *launches += 2;
   }
@@ -1498,9 +1524,7 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
   const uint32_t cut_blocks = (uint32_t)std::min<uint64_t>(full, (a.merge_tiles + S1_WARPS) / S1_WARPS);
   step1_cut_kernel<W><<<cut_blocks, S1_THREADS, 0, s>>>(a);
   ++*launches;
-  int dev = 0;
-  if (current_device(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
-  const uint64_t merge_full = (uint64_t)launch_state().merge_per_sm[dev][W == 4 ? 0 : (W == 8 ? 1 : 2)] * sm_count;
+  const uint64_t merge_full = (uint64_t)launch_state().merge_per_sm[dev][wi] * sm_count;
   step1_merge_kernel<W><<<(uint32_t)std::min<uint64_t>(std::max<uint64_t>(merge_full, 1), a.merge_tiles),
                           S1_THREADS, merge_smem_bytes<W>(), s>>>(a);
   ++*launches;
