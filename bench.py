@@ -772,35 +772,45 @@ def run_table(args):
     update = None
     if args.ingest:
         # Eq. 16's update rate for the table: its N_D delta rows over the time
-        # to insert them into every column (T_U: each column's delta ingest,
-        # columns with repeated data timed once) plus the batched merge (T_M)
-        per_src = {}
+        # to insert them into every column (T_U: one table ingest, the
+        # columns side by side) plus the batched merge (T_M)
+        n_d = TABLES[args.workload]["n_delta"]
+        vals = {}
+        ig_cols = []
         for j in mine:
             k = j % nsrc
-            if k in per_src:
-                continue
             d = srcs[k][1]
-            vals = d.delta_dict[d.delta_codes.long()]
-            nd = int(d.n_delta)
-            igd = dm.key_tensor_empty(max(nd, 1), d.w)
-            igc = torch.empty(max(nd, 1), dtype=torch.int32, device=f"cuda:{local}")
+            assert int(d.n_delta) == n_d
+            if k not in vals:
+                vals[k] = d.delta_dict[d.delta_codes.long()]
+            igd = dm.key_tensor_empty(max(n_d, 1), d.w)
+            igc = torch.empty(max(n_d, 1), dtype=torch.int32, device=f"cuda:{local}")
             igl = torch.zeros(1, dtype=torch.int64, device=f"cuda:{local}")
-            ictx_need = dm.dm_ingest_scratch_bytes(d.w, nd)
-            if ictx_need > ctx.arena_bytes:
-                ctx.reserve(ictx_need)
-            dm.dm_ingest_delta(ctx, d.w, vals, nd, igd, igc, igl, stream)
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
-            for a_, b_ in ev:
-                a_.record(stream)
-                dm.dm_ingest_delta(ctx, d.w, vals, nd, igd, igc, igl, stream)
-                b_.record(stream)
-            torch.cuda.synchronize()
-            per_src[k] = sorted(a_.elapsed_time(b_) for a_, b_ in ev)[2]
-        t_u = sum(per_src[j % nsrc] for j in mine)
+            ig_cols.append((d.w, vals[k], igd, igc, igl))
+        dm.dm_ingest_table(ctx, ig_cols, n_d, stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        for a_, b_ in ev:
+            a_.record(stream)
+            dm.dm_ingest_table(ctx, ig_cols, n_d, stream)
+            b_.record(stream)
+        torch.cuda.synchronize()
+        t_u = sorted(a_.elapsed_time(b_) for a_, b_ in ev)[2]
+        # each distinct column's ingest reproduces its delta partition
+        same, seen = True, set()
+        for j, (w_, _, igd, igc, igl) in zip(mine, ig_cols):
+            k = j % nsrc
+            if k in seen:
+                continue
+            seen.add(k)
+            d = srcs[k][1]
+            dl = int(igl.item())
+            same = same and dl == d.d and bool(torch.equal(igd[:dl], d.delta_dict)) and \
+                bool(torch.equal(igc[:n_d], d.delta_codes))
         t_m = t_batched / args.steps
-        n_d = TABLES[args.workload]["n_delta"]
         update = {"updates_per_s": n_d / ((t_u + t_m) / 1e3), "t_u_ms": t_u, "t_m_ms": t_m, "columns": len(mine),
-                  "definition": "N_D / (T_U + T_M), Eq. 16: T_U every column's delta ingest, T_M the batched merge"}
+                  "ingest": "dm_ingest_table: the table's columns side by side on the context's branches",
+                  "same_as_the_workload_deltas": same, "status": ctx.sync_status(),
+                  "definition": "N_D / (T_U + T_M), Eq. 16: T_U the table's delta ingest, T_M the batched merge"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # every distinct column data set once: the table repeats each of them

@@ -233,6 +233,28 @@ size_t dm_ingest_scratch_bytes(uint32_t value_bytes, uint64_t n);
 dm_status dm_ingest_delta(dm_ctx* ctx, uint32_t value_bytes, const void* values, uint64_t n, void* dict_out,
                           uint32_t* codes_out, uint64_t* d_dict_len, void* stream);
 
+/* One column of a table ingest: its width, the n appended values (device)
+ * and its outputs, as in dm_ingest_delta. */
+typedef struct {
+  uint32_t value_bytes;
+  const void* values;
+  void* dict_out;
+  uint32_t* codes_out;
+  uint64_t* d_dict_len;
+} dm_ingest_column;
+
+/* n rows appended to a table of ncols columns (Section 4: a row insert adds
+ * one value to every column's delta; the update rate of Eq. 16 counts rows),
+ * each column ingested exactly as dm_ingest_delta does.  The columns run
+ * concurrently on the context's side streams, round-robin over as many
+ * branches as a table merge uses, each branch with its own scratch region
+ * of the arena (dm_ingest_table_scratch_bytes); the call's stream waits for
+ * them all.  Every column is checked before anything is launched (DM_EINVAL
+ * for the first bad one; DM_ENOMEM when the arena is too small).
+ * Asynchronous. */
+size_t dm_ingest_table_scratch_bytes(const dm_ingest_column* cols, uint32_t ncols, uint64_t n);
+dm_status dm_ingest_table(dm_ctx* ctx, const dm_ingest_column* cols, uint32_t ncols, uint64_t n, void* stream);
+
 /* ---- allocation-free variant ---- */
 
 /* Largest |U_M| + |U_D| that dm_merge_dicts_noalloc accepts. */

@@ -304,40 +304,108 @@ extern "C" size_t dm_ingest_scratch_bytes(uint32_t value_bytes, uint64_t n) {
   return dm::round256(slots * 4) * 2 + dm::round256(n * 4) + dm::round256(tiles * 4 + 4);
 }
 
-extern "C" dm_status dm_ingest_delta(dm_ctx* ctx, uint32_t value_bytes, const void* values, uint64_t n,
-                                     void* dict_out, uint32_t* codes_out, uint64_t* d_dict_len, void* stream) {
-  const uint32_t w = value_bytes;
-  if (!ctx || (w != 4 && w != 8 && w != 16) || !d_dict_len || n > dm::IG_MAX_ROWS) return DM_EINVAL;
+namespace dm {
+namespace {
+
+// Argument checks of one column's ingest (no launch).
+dm_status ingest_check(uint32_t w, const void* values, uint64_t n, const void* dict_out, const uint32_t* codes_out,
+                       const uint64_t* d_dict_len) {
+  if ((w != 4 && w != 8 && w != 16) || !d_dict_len || n > IG_MAX_ROWS) return DM_EINVAL;
   if (n && (!values || !dict_out || !codes_out)) return DM_EINVAL;
   if (n && ((reinterpret_cast<uintptr_t>(values) | reinterpret_cast<uintptr_t>(dict_out)) & (w - 1))) return DM_EINVAL;
-  if (dm_ingest_scratch_bytes(w, n) > ctx->arena_bytes) return DM_ENOMEM;
-  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return DM_OK;
+}
+
+// One column's ingest on stream s with its scratch at `base`.
+dm_status ingest_column(dm_ctx* ctx, uint32_t w, const void* values, uint64_t n, void* dict_out, uint32_t* codes_out,
+                        uint64_t* d_dict_len, cudaStream_t s, void* base) {
   if (n == 0) return cudaMemsetAsync(d_dict_len, 0, 8, s) == cudaSuccess ? DM_OK : DM_ECUDA;
-  dm::IngestArgs a{};
+  IngestArgs a{};
   a.values = values;
   a.n = n;
   a.dict_out = dict_out;
   a.codes = codes_out;
   a.d_out = d_dict_len;
-  a.slots = dm::table_slots(n);
-  a.tiles = (uint32_t)((n + dm::IG_TILE - 1) / dm::IG_TILE);
-  char* p = static_cast<char*>(ctx->arena);
+  a.slots = table_slots(n);
+  a.tiles = (uint32_t)((n + IG_TILE - 1) / IG_TILE);
+  char* p = static_cast<char*>(base);
   a.table = reinterpret_cast<uint32_t*>(p);
-  p += dm::round256(a.slots * 4);
+  p += round256(a.slots * 4);
   a.slot_code = reinterpret_cast<uint32_t*>(p);
-  p += dm::round256(a.slots * 4);
+  p += round256(a.slots * 4);
   a.slot_of = reinterpret_cast<uint32_t*>(p);
-  p += dm::round256(n * 4);
+  p += round256(n * 4);
   a.tile_first = reinterpret_cast<uint32_t*>(p);
   a.status = ctx->status;
   if (cudaMemsetAsync(a.table, 0xFF, a.slots * 4, s) != cudaSuccess) return DM_ECUDA;
   cudaError_t e;
   switch (w) {
-    case 4: e = dm::launch_ingest<4>(a, s, ctx->sm_count, &ctx->launches); break;
-    case 8: e = dm::launch_ingest<8>(a, s, ctx->sm_count, &ctx->launches); break;
-    default: e = dm::launch_ingest<16>(a, s, ctx->sm_count, &ctx->launches); break;
+    case 4: e = launch_ingest<4>(a, s, ctx->sm_count, &ctx->launches); break;
+    case 8: e = launch_ingest<8>(a, s, ctx->sm_count, &ctx->launches); break;
+    default: e = launch_ingest<16>(a, s, ctx->sm_count, &ctx->launches); break;
   }
   if (e != cudaSuccess) ctx->last_error = e;
   return e == cudaSuccess ? DM_OK : DM_ECUDA;
+}
+
+}  // namespace
+}  // namespace dm
+
+extern "C" dm_status dm_ingest_delta(dm_ctx* ctx, uint32_t value_bytes, const void* values, uint64_t n,
+                                     void* dict_out, uint32_t* codes_out, uint64_t* d_dict_len, void* stream) {
+  if (!ctx) return DM_EINVAL;
+  const dm_status st = dm::ingest_check(value_bytes, values, n, dict_out, codes_out, d_dict_len);
+  if (st != DM_OK) return st;
+  if (dm_ingest_scratch_bytes(value_bytes, n) > ctx->arena_bytes) return DM_ENOMEM;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  return dm::ingest_column(ctx, value_bytes, values, n, dict_out, codes_out, d_dict_len,
+                           static_cast<cudaStream_t>(stream), ctx->arena);
+}
+
+// Branches of a table ingest: the context's side streams (as many as a table
+// merge uses), each with its own scratch region.
+static uint32_t ingest_branches(const dm_ctx* ctx, uint32_t ncols) {
+  uint32_t b = ctx->tuning.table_branches ? ctx->tuning.table_branches : dm_ctx::kTableBranches;
+  if (b > dm_ctx::kTableStreams) b = dm_ctx::kTableStreams;
+  return ncols < b ? (ncols ? ncols : 1) : b;
+}
+
+extern "C" size_t dm_ingest_table_scratch_bytes(const dm_ingest_column* cols, uint32_t ncols, uint64_t n) {
+  (void)cols;
+  const size_t region = (dm_ingest_scratch_bytes(4, n) + 255) & ~(size_t)255;
+  return region * (ncols < dm_ctx::kTableStreams ? (ncols ? ncols : 1) : dm_ctx::kTableStreams);
+}
+
+extern "C" dm_status dm_ingest_table(dm_ctx* ctx, const dm_ingest_column* cols, uint32_t ncols, uint64_t n,
+                                     void* stream) {
+  if (!ctx || (ncols && !cols)) return DM_EINVAL;
+  for (uint32_t c = 0; c < ncols; ++c) {
+    const dm_status st = dm::ingest_check(cols[c].value_bytes, cols[c].values, n, cols[c].dict_out,
+                                          cols[c].codes_out, cols[c].d_dict_len);
+    if (st != DM_OK) return st;
+  }
+  if (ncols == 0) return DM_OK;
+  const uint32_t S = ingest_branches(ctx, ncols);
+  const size_t region = (dm_ingest_scratch_bytes(4, n) + 255) & ~(size_t)255;
+  if (region * S > ctx->arena_bytes) return DM_ENOMEM;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return DM_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // columns round-robin over the side streams, which start after earlier
+  // work on s and which s waits for at the end
+  if (cudaEventRecord(ctx->fork, s) != cudaSuccess) return DM_ECUDA;
+  for (uint32_t i = 0; i < S; ++i)
+    if (cudaStreamWaitEvent(ctx->side[i], ctx->fork, 0) != cudaSuccess) return DM_ECUDA;
+  dm_status st = DM_OK;
+  for (uint32_t c = 0; c < ncols && st == DM_OK; ++c) {
+    const uint32_t i = c % S;
+    st = dm::ingest_column(ctx, cols[c].value_bytes, cols[c].values, n, cols[c].dict_out, cols[c].codes_out,
+                           cols[c].d_dict_len, ctx->side[i], static_cast<char*>(ctx->arena) + (size_t)i * region);
+  }
+  // join every branch whatever happened, so that no work is left unordered
+  for (uint32_t i = 0; i < S; ++i) {
+    if (cudaEventRecord(ctx->join[i], ctx->side[i]) != cudaSuccess ||
+        cudaStreamWaitEvent(s, ctx->join[i], 0) != cudaSuccess)
+      st = DM_ECUDA;
+  }
+  return st;
 }

@@ -52,7 +52,7 @@ EXPORTS = [
     "dm_tune_candidates", "dm_autotune_column", "dm_reencode_search", "dm_ingest_scratch_bytes",
     "dm_ingest_delta", "dm_set_wait_test", "dm_server_add_online_table", "dm_server_insert",
     "dm_server_pause", "dm_server_online_view", "dm_online_simulate", "dm_server_online_copy",
-    "dm_column_digest",
+    "dm_column_digest", "dm_ingest_table_scratch_bytes", "dm_ingest_table",
 ]
 
 
@@ -149,6 +149,12 @@ class OnlineColumn(ctypes.Structure):
     _fields_ = [("value_bytes", ctypes.c_uint32), ("main_dict", ctypes.c_void_p),
                 ("main_dict_len", ctypes.c_uint64), ("main_packed", ctypes.c_void_p),
                 ("main_bits", ctypes.c_uint32)]
+
+
+class IngestColumn(ctypes.Structure):
+    """dm_ingest_column: one column of a table ingest."""
+    _fields_ = [("value_bytes", ctypes.c_uint32), ("values", ctypes.c_void_p), ("dict_out", ctypes.c_void_p),
+                ("codes_out", ctypes.c_void_p), ("d_dict_len", ctypes.c_void_p)]
 
 
 class OnlineConfig(ctypes.Structure):
@@ -272,6 +278,8 @@ def _load():
             "dm_reencode_search": ([vp, pin, pout, vp], i32),
             "dm_ingest_scratch_bytes": ([u32, u64], sz),
             "dm_ingest_delta": ([vp, u32, vp, u64, vp, vp, vp, vp], i32),
+            "dm_ingest_table_scratch_bytes": ([vp, u32, u64], sz),
+            "dm_ingest_table": ([vp, vp, u32, u64, vp], i32),
             "dm_set_wait_test": ([vp, u32, u32], i32),
             "dm_server_add_online_table": ([vp, u32, u32, ctypes.POINTER(OnlineColumn),
                                             ctypes.POINTER(OnlineConfig)], i32),
@@ -525,6 +533,19 @@ def dm_ingest_delta(ctx: Context, w: int, values, n: int, dict_out, codes_out, d
         ctx.reserve(need)
     _check(_load().dm_ingest_delta(ctx.handle, w, _ptr(values), n, _ptr(dict_out), _ptr(codes_out), _ptr(d_len),
                                    _stream(stream)), "dm_ingest_delta", ctx)
+
+
+def dm_ingest_table(ctx: Context, cols, n: int, stream=None):
+    """n rows appended to a table: cols is a list of (w, values, dict_out,
+    codes_out, d_len) per column, each ingested as dm_ingest_delta does, the
+    columns side by side on the context's branches."""
+    arr = (IngestColumn * max(len(cols), 1))()
+    for k, (w, values, dict_out, codes_out, d_len) in enumerate(cols):
+        arr[k] = IngestColumn(w, _ptr(values), _ptr(dict_out), _ptr(codes_out), _ptr(d_len))
+    need = int(_load().dm_ingest_table_scratch_bytes(arr, len(cols), n))
+    if need > ctx.arena_bytes:
+        ctx.reserve(need)
+    _check(_load().dm_ingest_table(ctx.handle, arr, len(cols), n, _stream(stream)), "dm_ingest_table", ctx)
 
 
 def dm_merge_table(ctx: Context, cins, couts, stream=None, flags: int = 0):

@@ -73,3 +73,48 @@ def test_ingest_empty(ctx):
     dm.dm_ingest_delta(ctx, 8, None, 0, None, None, dlen)
     torch.cuda.synchronize()
     assert int(dlen.item()) == 0
+
+
+def test_ingest_table_equals_each_column_alone(ctx):
+    """A table ingest of 11 columns (more than the eight branches, so
+    branches take several columns in turn and reuse their scratch) of every
+    width and duplicate density: each column's D_dict, codes and |D_dict|
+    equal the oracle's ingest of that column."""
+    import torch
+    n = 300_007
+    shapes = [(4, 7), (8, 20_000), (16, 300_007), (8, 1), (4, 150_000), (16, 37), (8, 299_000), (4, 2),
+              (16, 5_000), (8, 64), (4, 300_007)]
+    cols, wants, outs = [], [], []
+    for k, (w, distinct) in enumerate(shapes):
+        vals = _values(w, n, distinct, 900 + k)
+        if distinct == n:
+            vals = synth.dictionary(synth.subseed(k, w), w, n)[np.random.default_rng(k).permutation(n)]
+        wants.append(oracle.ingest_delta(w, vals))
+        t = dm.to_device(vals)
+        dd = dm.key_tensor_empty(n, w)
+        codes = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        dlen = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        cols.append((w, t, dd, codes, dlen))
+        outs.append((w, dd, codes, dlen))
+    dm.dm_ingest_table(ctx, cols, n)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_OK
+    for (w, dd, codes, dlen), (want_dd, want_codes) in zip(outs, wants):
+        d = int(dlen.item())
+        assert d == want_dd.shape[0]
+        assert np.array_equal(dm.to_host(dd[:d], dm.key_np_dtype(w)), want_dd)
+        assert np.array_equal(dm.to_host(codes, np.uint32), want_codes)
+
+
+def test_ingest_table_rejects_a_bad_column_before_launching():
+    import torch
+    from paper_1109_6885_gb300 import build
+    build.build()
+    c = dm.Context(0, 1 << 20)
+    good = dm.key_tensor_empty(16, 8)
+    out = torch.zeros(16, dtype=torch.int32, device="cuda")
+    dlen = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(dm.DmError) as e:
+        dm.dm_ingest_table(c, [(8, good, good, out, dlen), (3, good, good, out, dlen)], 16)
+    assert e.value.status == dm.DM_EINVAL
+    c.close()
