@@ -100,7 +100,7 @@ def test_rows_inserted_during_a_merge_land_in_the_next_version():
 
     mid_merge = 0
     for k in range(3):
-        va, vb = 2 * k + 1, 2 * k + 2                  # the versions of this round's two merges
+        va, vb = 2 * k + 1, 2 * k + 2                  # the versions of this pass's two merges
         a = [batch(c, 300_000, 100 * k + j) for j, c in enumerate(cols)]
         b = [batch(c, 50_000, 100 * k + 50 + j) for j, c in enumerate(cols)]
         adev, bdev = [dm.to_device(x) for x in a], [dm.to_device(x) for x in b]
