@@ -26,6 +26,14 @@ struct Step1Args {
   uint32_t* sort_lb;         // [W][sort_tiles][256] look-back words (zeroed)
   uint32_t sort_tiles;
   uint32_t hist_blocks;      // set by the launcher
+  // two-level partition of a large sort (bins of the two most significant
+  // varying bytes), laid out with the zeroed bookkeeping when d can use it,
+  // else nullptr: bin counts, bin cursors, then the bins' offsets
+  // (JOINT_BINS + 1 words) followed by the decision word
+  uint32_t* jhist;
+  uint32_t* jcur;
+  uint32_t* joff;
+  uint32_t jgroup;           // bins per group of the in-place group sorts (set by the launcher)
   void** final_slot;         // optional: [0] sorted keys, [1] perm (for copy-out)
   // Step 1(b) + 2(a): merge with the main dictionary
   const void* a;             // U_M
@@ -65,6 +73,10 @@ cudaError_t step1_prepare();
 uint32_t step1_capacity(uint32_t w, uint32_t sm_count);
 
 uint32_t sort_tiles(uint64_t d);
+constexpr uint32_t JOINT_BINS = 1u << 16;
+// Delta sizes past which a top-byte partition cannot leave every bucket
+// within the shared-memory sort: the two-level partition's scratch exists.
+constexpr uint64_t JOINT_MIN_KEYS = 256ull * 2048;
 uint32_t merge_tiles(uint64_t n, uint32_t w);
 // 32-bit words of bookkeeping to zero before a Step 1 launch that merges
 // n_merge dictionary entries and sorts d_sort keys of w bytes.

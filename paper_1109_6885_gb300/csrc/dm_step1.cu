@@ -1231,6 +1231,16 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
 // a byte the plan skips, or the passes when the plan partitions on the top
 // byte instead (and the reverse), return at once.
 
+// The byte below `top` that varies (-1: none), and whether a large sort
+// took the two-level partition (its scan's decision word).
+__device__ __forceinline__ int byte_below(uint32_t run, int top) {
+  const uint32_t lower = run & ((1u << top) - 1u);
+  return lower ? 31 - __clz(lower) : -1;
+}
+__device__ __forceinline__ bool joint_chosen(const Step1Args& a) {
+  return a.joff != nullptr && __ldcg(a.joff + JOINT_BINS + 1) != 0u;
+}
+
 template <int W>
 __global__ void __launch_bounds__(S1_THREADS, SORT_BLOCKS_MIN) step1_hist_kernel(Step1Args a) {
   extern __shared__ __align__(16) unsigned char dsmem[];
@@ -1244,7 +1254,7 @@ __global__ void __launch_bounds__(S1_THREADS, SORT_BLOCKS_MIN) step1_pass_kernel
   uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(SortPhase<W>) + 15) / 16 * 16);
   bool msd = false;
   const uint32_t run = plan_phase<W>(a, SP.plan, s_wsum, &msd);
-  if (msd || !((run >> pass) & 1u)) return;
+  if (msd || !((run >> pass) & 1u) || joint_chosen(a)) return;
   const int e = __popc(run & ((1u << pass) - 1u));
   for (;;) {
     if (threadIdx.x == 0) SP.s.next = atomicAdd(a.barriers + pass, 1u);
@@ -1266,6 +1276,122 @@ __global__ void __launch_bounds__(S1_THREADS, SORT_BLOCKS_MIN) step1_msd_kernel(
   if (!msd) return;
   const int top = 31 - __clz(run);
   for (uint32_t t = blockIdx.x; t < a.sort_tiles; t += gridDim.x) msd_tile<W>(a, top, t, SP.plan, SP.s);
+}
+
+// ---- two-level partition of a large sort (split form)
+// When the plan's top varying byte leaves a bucket above BK_CAP keys (more
+// than 256 * BK_CAP keys in all make that certain), the keys are binned on
+// their two most significant varying bytes instead: a histogram of the
+// JOINT_BINS bins, one block's scan of it (which also checks that every bin
+// fits the shared-memory sort, else the LSD passes run as before), one
+// scatter into the bins, and in-place sorts of groups of consecutive bins by
+// (key, insertion code).  Three passes over the keys instead of one per
+// varying byte.
+static_assert(JOINT_MIN_KEYS == 256ull * BK_CAP, "a top-byte bucket above BK_CAP keys");
+
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS, SORT_BLOCKS_MIN) step1_jhist_kernel(Step1Args a) {
+  using K = typename KeyOf<W>::T;
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  SortPhase<W>& SP = *reinterpret_cast<SortPhase<W>*>(dsmem);
+  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(SortPhase<W>) + 15) / 16 * 16);
+  bool msd = false;
+  const uint32_t run = plan_phase<W>(a, SP.plan, s_wsum, &msd);
+  const int top = 31 - __clz(run), nxt = byte_below(run, top);
+  if (msd || nxt < 0) return;
+  const K* keys = static_cast<const K*>(a.in_keys);
+  const uint64_t stride = (uint64_t)gridDim.x * S1_THREADS;
+  for (uint64_t i = (uint64_t)blockIdx.x * S1_THREADS + threadIdx.x; i < a.d; i += stride) {
+    const K k = load_key(keys + i);
+    atomicAdd(&a.jhist[(key_digit(k, top) << 8) | key_digit(k, nxt)], 1u);
+  }
+}
+
+// One block: the bins' offsets and the decision (every bin at most BK_CAP).
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS) step1_jscan_kernel(Step1Args a) {
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  SortPhase<W>& SP = *reinterpret_cast<SortPhase<W>*>(dsmem);
+  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(SortPhase<W>) + 15) / 16 * 16);
+  bool msd = false;
+  const uint32_t run = plan_phase<W>(a, SP.plan, s_wsum, &msd);
+  const int top = 31 - __clz(run), nxt = byte_below(run, top);
+  if (msd || nxt < 0) return;   // the decision word stays zero
+  constexpr uint32_t PER = JOINT_BINS / S1_THREADS;
+  const uint32_t b0 = threadIdx.x * PER;
+  uint32_t sum = 0, mx = 0;
+  for (uint32_t q = 0; q < PER; ++q) {
+    const uint32_t c = a.jhist[b0 + q];
+    sum += c;
+    mx = max(mx, c);
+  }
+  uint32_t total = 0;
+  uint32_t ex = block_excl_scan(sum, s_wsum, &total);
+  for (uint32_t q = 0; q < PER; ++q) {
+    a.joff[b0 + q] = ex;
+    ex += a.jhist[b0 + q];
+  }
+  const bool fits = !__syncthreads_or(mx > BK_CAP);
+  if (threadIdx.x == 0) {
+    a.joff[JOINT_BINS] = total;
+    a.joff[JOINT_BINS + 1] = fits && (uint64_t)total == a.d ? 1u : 0u;
+  }
+}
+
+// Every key to its bin (a cursor per bin), in the first ping-pong buffer.
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS, SORT_BLOCKS_MIN) step1_jscatter_kernel(Step1Args a) {
+  using K = typename KeyOf<W>::T;
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  if (!joint_chosen(a)) return;
+  SortPhase<W>& SP = *reinterpret_cast<SortPhase<W>*>(dsmem);
+  uint32_t* s_wsum = reinterpret_cast<uint32_t*>(dsmem + (sizeof(SortPhase<W>) + 15) / 16 * 16);
+  bool msd = false;
+  const uint32_t run = plan_phase<W>(a, SP.plan, s_wsum, &msd);
+  const int top = 31 - __clz(run), nxt = byte_below(run, top);
+  if (nxt < 0) return;
+  const K* keys = static_cast<const K*>(a.in_keys);
+  K* dst_k = static_cast<K*>(a.keys[0]);
+  uint32_t* dst_v = a.vals[0];
+  const uint64_t stride = (uint64_t)gridDim.x * S1_THREADS;
+  for (uint64_t i = (uint64_t)blockIdx.x * S1_THREADS + threadIdx.x; i < a.d; i += stride) {
+    const K k = load_key(keys + i);
+    const uint32_t bin = (key_digit(k, top) << 8) | key_digit(k, nxt);
+    const uint64_t pos = (uint64_t)__ldg(a.joff + bin) + atomicAdd(&a.jcur[bin], 1u);
+    if (pos < a.d) {
+      dst_k[pos] = k;
+      dst_v[pos] = (uint32_t)i;
+    } else {
+      flag_status(a.status, ST_INTERNAL);
+    }
+  }
+}
+
+// Groups of jgroup consecutive bins sorted in place: a group of at most
+// BK_CAP keys at once (its bins are in key order, so the group's range is),
+// a larger one bin by bin (each at most BK_CAP).
+template <int W>
+__global__ void __launch_bounds__(S1_THREADS, 2) step1_jgroup_kernel(Step1Args a) {
+  using K = typename KeyOf<W>::T;
+  extern __shared__ __align__(16) unsigned char dsmem[];
+  if (!joint_chosen(a)) return;
+  Step1Smem<W>& U = *reinterpret_cast<Step1Smem<W>*>(dsmem);
+  K* k0 = static_cast<K*>(a.keys[0]);
+  uint32_t* v0 = a.vals[0];
+  const uint32_t G = a.jgroup ? a.jgroup : 1u;
+  const uint32_t ngroups = (JOINT_BINS + G - 1) / G;
+  for (uint32_t g = blockIdx.x; g < ngroups; g += gridDim.x) {
+    const uint32_t b0 = g * G, b1 = min(b0 + G, JOINT_BINS);
+    const uint32_t lo = __ldg(a.joff + b0), n = __ldg(a.joff + b1) - lo;
+    if (n <= BK_CAP) {
+      if (n > 1 && (uint64_t)lo + n <= a.d) bucket_sort<W>(k0, v0, lo, n, true, k0, v0, U.bp.b);
+      continue;
+    }
+    for (uint32_t b = b0; b < b1; ++b) {
+      const uint32_t o = __ldg(a.joff + b), nb = __ldg(a.joff + b + 1) - o;
+      if (nb > 1 && nb <= BK_CAP && (uint64_t)o + nb <= a.d) bucket_sort<W>(k0, v0, o, nb, true, k0, v0, U.bp.b);
+    }
+  }
 }
 
 // The buckets of the top-byte partition, each sorted in shared memory; and
@@ -1293,7 +1419,7 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_bucket_kernel(Step1Args a
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const bool last_odd = !msd && ((__popc(run) - 1) & 1);
+    const bool last_odd = !msd && !joint_chosen(a) && ((__popc(run) - 1) & 1);
     a.final_slot[0] = last_odd ? a.keys[1] : a.keys[0];
     a.final_slot[1] = last_odd ? a.vals[1] : a.vals[0];
   }
@@ -1405,8 +1531,11 @@ int prepare_w(cudaError_t* err) {
   cudaError_t e = cudaFuncSetAttribute(step1_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(step1_bucket_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(step1_jgroup_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   for (const void* fn : {(const void*)step1_hist_kernel<W>, (const void*)step1_pass_kernel<W>,
-                         (const void*)step1_msd_kernel<W>})
+                         (const void*)step1_msd_kernel<W>, (const void*)step1_jhist_kernel<W>,
+                         (const void*)step1_jscan_kernel<W>, (const void*)step1_jscatter_kernel<W>})
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem_bytes<W>());
   int sort_per_sm = 0;
@@ -1512,6 +1641,19 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
     step1_hist_kernel<W><<<h.hist_blocks, S1_THREADS, ssm, s>>>(h);
     ++*launches;
     const uint32_t sort_grid = (uint32_t)std::min<uint64_t>(sort_full, a.sort_tiles);
+    if (a.jhist) {
+      // the two-level partition; when the plan or its bins rule it out, its
+      // kernels return at once and the LSD passes below run
+      Step1Args j = a;
+      const uint64_t per_bin = std::max<uint64_t>(1, a.d / JOINT_BINS);
+      j.jgroup = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(JOINT_BINS, (BK_CAP / 2) / per_bin));
+      const uint32_t ngroups = (JOINT_BINS + j.jgroup - 1) / j.jgroup;
+      step1_jhist_kernel<W><<<sort_grid, S1_THREADS, ssm, s>>>(j);
+      step1_jscan_kernel<W><<<1, S1_THREADS, ssm, s>>>(j);
+      step1_jscatter_kernel<W><<<sort_grid, S1_THREADS, ssm, s>>>(j);
+      step1_jgroup_kernel<W><<<(uint32_t)std::min<uint64_t>(full, ngroups), S1_THREADS, smem, s>>>(j);
+      *launches += 4;
+    }
     for (int p = 0; p < W; ++p) {
       step1_pass_kernel<W><<<sort_grid, S1_THREADS, ssm, s>>>(a, p);
       ++*launches;
@@ -1558,7 +1700,8 @@ uint32_t merge_tiles(uint64_t n, uint32_t w) { return (uint32_t)((n + mg_tile(w)
 uint64_t step1_zeroed_words(uint32_t w, uint64_t n_merge, uint64_t d) {
   // merge look-back (64-bit words), barrier counters, digit histograms,
   // sort look-back
-  return 2ull * merge_tiles(n_merge, w) + S1_BARRIERS + (d ? (uint64_t)w * 256 + (uint64_t)w * sort_tiles(d) * 256 : 0);
+  return 2ull * merge_tiles(n_merge, w) + S1_BARRIERS + (d ? (uint64_t)w * 256 + (uint64_t)w * sort_tiles(d) * 256 : 0) +
+         (d > JOINT_MIN_KEYS ? 3ull * JOINT_BINS + 2 : 0);
 }
 
 void step1_layout(uint32_t w, uint64_t n_merge, uint64_t d, uint32_t* zero, Step1Args* a) {
@@ -1570,6 +1713,13 @@ void step1_layout(uint32_t w, uint64_t n_merge, uint64_t d, uint32_t* zero, Step
   a->hist = z;
   a->sort_tiles = sort_tiles(d);
   a->sort_lb = z + (uint64_t)w * 256;
+  a->jhist = a->jcur = a->joff = nullptr;
+  if (d > JOINT_MIN_KEYS) {
+    uint32_t* j = a->sort_lb + (uint64_t)w * sort_tiles(d) * 256;
+    a->jhist = j;
+    a->jcur = j + JOINT_BINS;
+    a->joff = j + 2 * JOINT_BINS;   // JOINT_BINS + 1 offsets, then the decision word
+  }
 }
 
 cudaError_t launch_step1(uint32_t w, const Step1Args& a, cudaStream_t s, uint32_t sm_count, uint64_t* launches) {

@@ -104,6 +104,66 @@ def test_sort_skewed_lower_bytes(ctx, w, lowbits):
     assert np.array_equal(dm.to_host(perm, np.uint32), perm_ref)
 
 
+def _sort_check(ctx, w, dd):
+    import torch
+    d = dd.shape[0]
+    ctx.reserve(max(ctx.arena_bytes, 256 << 20))     # two key buffers and their codes
+    ud_ref, perm_ref = oracle.sort_delta(w, dd)
+    ud = dm.key_tensor_empty(d, w)
+    perm = torch.empty(d, dtype=torch.int32, device="cuda")
+    dm.dm_sort_delta(ctx, w, dm.to_device(dd), d, ud, perm)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_OK
+    assert np.array_equal(dm.to_host(ud, kd(w)), ud_ref)
+    assert np.array_equal(dm.to_host(perm, np.uint32), perm_ref)
+
+
+@pytest.mark.parametrize("w", [4, 8, 16])
+@pytest.mark.parametrize("case", ["uniform", "crowded_bin", "one_byte", "two_bytes"])
+def test_sort_large_deltas(ctx, w, case):
+    """Sorts of 1.6M keys take the split form.  Uniform keys bin on their two
+    most significant varying bytes (65,536 bins of about 25 keys) and sort
+    groups of bins in place; one bin of 5,000 keys (above what a block sorts
+    in shared memory) sends the sort back to the LSD passes; keys varying in
+    one byte only, or in two, bin on what varies.  Repeats inside D_dict
+    throughout."""
+    rng = np.random.default_rng(600 + w + len(case))
+    d = 1_600_003
+    t = kd(w)
+    if case == "uniform":
+        dd = synth.dictionary(synth.subseed(d, w), w, d)[rng.permutation(d)]
+    elif case == "crowded_bin":
+        dd = synth.dictionary(synth.subseed(d + 1, w), w, d)[rng.permutation(d)]
+        pick = rng.choice(d, 5000, replace=False)
+        if w == 16:
+            dd[pick, 0] = (dd[pick, 0] & np.uint64(0x0000FFFFFFFFFFFF)) | np.uint64(0xABCD) << np.uint64(48)
+        else:
+            hi = t(8 * w - 16)
+            mask = t((1 << (8 * w - 16)) - 1)
+            dd[pick] = (dd[pick] & mask) | (t(0xABCD) << hi)
+    elif case == "one_byte":
+        dd = rng.integers(0, 256, d).astype(t) if w < 16 else np.stack(
+            [np.zeros(d, np.uint64), rng.integers(0, 256, d).astype(np.uint64)], axis=1)
+    else:   # two varying bytes, far apart
+        lo = rng.integers(0, 256, d)
+        top = rng.integers(0, 256, d)
+        if w == 16:
+            dd = np.stack([top.astype(np.uint64) << np.uint64(40), lo.astype(np.uint64) << np.uint64(8)], axis=1)
+        else:
+            dd = (top.astype(t) << t(8 * w - 8)) | (lo.astype(t) << t(8))
+    if case in ("uniform", "crowded_bin"):
+        dd[rng.integers(0, d, d // 10)] = dd[rng.integers(0, d, d // 10)]
+    _sort_check(ctx, w, np.ascontiguousarray(dd))
+
+
+def test_merge_column_with_a_large_delta(ctx):
+    """A whole column whose 1.9M-value delta takes the two-level partition."""
+    col = synth.make_column(synth.ColumnSpec(n_main=3_000_000, m=2_500_000, w=8, n_delta=4_000_000, f_new=0.5,
+                                             dist="uniform", seed=611))
+    assert col.delta_dict.shape[0] > 1_300_000
+    assert_parity(ctx, col)
+
+
 # ------------------------------------------------------------------ Step 1(b) + 2(a)
 
 @pytest.mark.parametrize("w", [4, 8, 16])
