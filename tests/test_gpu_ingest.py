@@ -118,3 +118,13 @@ def test_ingest_table_rejects_a_bad_column_before_launching():
         dm.dm_ingest_table(c, [(8, good, good, out, dlen), (3, good, good, out, dlen)], 16)
     assert e.value.status == dm.DM_EINVAL
     c.close()
+
+
+def test_ingest_table_of_no_rows_sets_every_length_to_zero(ctx):
+    import torch
+    lens = [torch.full((1,), -1, dtype=torch.int64, device="cuda") for _ in range(3)]
+    dm.dm_ingest_table(ctx, [(w, None, None, None, dl) for w, dl in zip((4, 8, 16), lens)], 0)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == dm.DM_OK
+    assert [int(dl.item()) for dl in lens] == [0, 0, 0]
+    dm.dm_ingest_table(ctx, [], 0)      # no columns: nothing to do
