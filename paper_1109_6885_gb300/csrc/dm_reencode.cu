@@ -41,9 +41,13 @@ namespace {
 constexpr uint32_t RE_STAGES_MAX = 4;
 constexpr uint32_t RE_TILE = 1024;          // codes per warp tile
 constexpr uint32_t RE_XSMEM_MAX = 16384;    // X_M entries staged in shared memory at most
-// Above this many main codes X_M (4 bytes a code) is unlikely to stay in L2
-// next to the streams, and the directory's crowded buckets read a byte table.
-constexpr uint64_t RE_X8_MIN_CODES = 8u << 20;
+// Above this many main codes X_M (4 bytes a code, 46 MB and more) starts to
+// lose its place in L2 next to the streams, and the directory's crowded
+// buckets read a byte table.  Below it a crowded code's X_M read is cheaper
+// than the byte table's path (and Step 1 skips building the table): at 10M
+// codes the merge is 10-50% faster without it, at 16M with dense steps 14%
+// slower.
+constexpr uint64_t RE_X8_MIN_CODES = 11u << 20;
 // Input widths that can carry that many codes (the byte-table path is
 // compiled into their kernels only).
 constexpr bool RE_X8_B(int b) { return (1ull << b) > RE_X8_MIN_CODES; }

@@ -68,8 +68,8 @@ FORCED_CASES = {
     # directory of X_M's steps (m above the table) from 2^20 main rows
     "directory": dict(n_main=1_500_003, m=100_000, w=8, n_delta=15_001, f_new=0.3, dist="zipf", zipf_s=1.0),
     "wide-keys": dict(n_main=1_100_001, m=60_000, w=16, n_delta=40_000, f_new=0.5, dist="uniform"),
-    # byte table for crowded directory buckets (above 2^23 main codes)
-    "byte-table": dict(n_main=10_000_000, m=9_000_000, w=8, n_delta=1_000_000, f_new=0.5, dist="zipf",
+    # byte table for crowded directory buckets (above 11 * 2^20 main codes)
+    "byte-table": dict(n_main=10_000_000, m=12_000_000, w=8, n_delta=1_000_000, f_new=0.5, dist="zipf",
                        zipf_s=0.8),
     "delta-only": dict(n_main=0, m=0, w=8, n_delta=200_003, f_new=1.0, dist="uniform"),
 }

@@ -635,7 +635,7 @@ def test_merge_repeats_bulk_copy_ring(ctx, flags):
 
 
 def test_reencode_byte_table(ctx):
-    """Above 8M main codes the directory's crowded buckets read a byte table of c[i] - base:
+    """Above 11 * 2^20 main codes the directory's crowded buckets read a byte table of c[i] - base:
     12M codes with 60k new values (most buckets crowded), plus one insertion point with 300
     new values (more than a byte holds: that bucket reads X_M)."""
     import torch
@@ -665,8 +665,8 @@ def test_reencode_byte_table(ctx):
 
 
 def test_merge_column_byte_table(ctx):
-    """A whole merge whose X_M (9M values, 450k new) takes the byte table."""
-    spec = synth.ColumnSpec(n_main=10_000_000, m=9_000_000, w=8, n_delta=1_000_000, f_new=0.5,
+    """A whole merge whose X_M (12M values, 450k new) takes the byte table."""
+    spec = synth.ColumnSpec(n_main=10_000_000, m=12_000_000, w=8, n_delta=1_000_000, f_new=0.5,
                             dist="zipf", zipf_s=0.8, seed=synth.column_seed(7, 1))
     col = synth.make_column(spec)
     ref = assert_parity(ctx, col)
