@@ -200,7 +200,8 @@ dm_status dm_merge_dicts(dm_ctx* ctx, uint32_t value_bytes, const void* main_dic
  * entries must be < 2^(*d_bits).  The context's arena holds the lookup
  * structures built on the way when it has room for them: the 64 KiB
  * directory of X_M's steps, then its byte table (m bytes, above 11 * 2^20
- * main codes) or, above 2^24 main codes, the global directory (8 bytes per 2^s
+ * main codes; filled and read only when X_M's steps average two or more a
+ * directory bucket) or, above 2^24 main codes, the global directory (8 bytes per 2^s
  * codes, s >= 6, at most 16 MiB); without room X_M is gathered directly. */
 dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bits,
                       uint64_t n_main, const uint32_t* delta_codes, uint64_t n_delta,
@@ -565,7 +566,7 @@ typedef struct {
 #define DM_STAGE_AUTO 0u     /* X_M lookup: library rule (shared memory from 2^20 main rows) */
 #define DM_STAGE_SMEM 1u     /* X_M in shared memory (table or directory of its steps) when it fits */
 #define DM_STAGE_GLOBAL 2u   /* X_M gathered through L1/L2 (no directory of its steps) */
-#define DM_X8_AUTO 0u        /* byte table for crowded directory buckets above 11 * 2^20 main codes */
+#define DM_X8_AUTO 0u        /* byte table for crowded directory buckets above 11 * 2^20 main codes (dense steps) */
 #define DM_X8_OFF 1u         /* no byte table: crowded buckets read X_M */
 
 /* Launch choices for one column class (0 = library default). */

@@ -211,9 +211,9 @@ __host__ __device__ __forceinline__ uint32_t smem_bytes(const Layout& L, uint32_
 __global__ void xdir_build_kernel(const uint32_t* __restrict__ xm, uint32_t m, uint32_t s, uint32_t R,
                                   uint32_t* __restrict__ dir, uint8_t* __restrict__ x8) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-  for (uint32_t b = t; b < R; b += nt) dir[b] = xdir_entry<false>(xm, m, s, b, x8 != nullptr);
-  if (x8)
-    for (uint32_t i = t; i < m; i += nt) x8[i] = xdir_x8<false>(xm, s, i);
+  const bool use_x8 = x8 != nullptr && xdir_x8_pays<false>(xm, m, R);
+  for (uint32_t b = t; b < R; b += nt) dir[b] = xdir_entry<false>(xm, m, s, b, use_x8);
+  if (use_x8) xdir_x8_fill<false>(xm, m, s, x8, t, nt);
 }
 
 // The global directory from the finished X_M: per bucket of 2^s codes the
@@ -274,6 +274,9 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32, RE_BLOCKS_MIN(B)) reencode_
   const uint32_t dshift = L.dir_shift, dmask = (1u << L.dir_shift) - 1u;
   const uint64_t stream_policy = policy_evict_first();   // the packed streams pass through once
 
+  // the byte table is read only where its builder wrote it: the same density
+  // rule over the finished X_M decides on both sides
+  const bool x8_on = RE_X8_B(B) && xmode == 2 && a.x8 != nullptr && xdir_x8_pays<false>(a.xm, a.m, L.x_entries);
   if (xmode == 1 || xmode == 2) {
     const uint32_t* src = xmode == 1 ? a.xm : a.xdir;
     for (uint32_t i = threadIdx.x; i < L.x_entries; i += blockDim.x) s_x[i] = __ldg(src + i);
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(RE_WARPS_MAX * 32, RE_BLOCKS_MIN(B)) reencode_
         // codes in buckets with several steps read X_M, or the byte table
         // where there is one (an X_M too large to stay in L2)
         if (__any_sync(0xFFFFFFFFu, many != 0)) {
-          if (!RE_X8_B(B) || a.x8 == nullptr) {
+          if (!x8_on) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
               if ((many >> j) & 1u) x[j] = __ldg(a.xm + c[j]);
@@ -661,7 +664,7 @@ cudaError_t launch_xdir(const ReencodePlan& plan, const ReencodeArgs& a, cudaStr
   ReencodePlanImpl P;
   memcpy(&P, plan.storage, sizeof(P));
   if (P.L.x_mode != 2) return cudaSuccess;
-  const uint32_t work = a.x8 ? a.m : P.L.x_entries;
+  const uint32_t work = std::max<uint32_t>(P.L.x_entries, a.x8 ? (uint32_t)((a.m + 3) / 4) : 0u);
   uint32_t blocks = (work + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   xdir_build_kernel<<<blocks, 256, 0, s>>>(a.xm, a.m, P.L.dir_shift, P.L.x_entries, a.xdir, a.x8);

@@ -1206,11 +1206,12 @@ __global__ void __launch_bounds__(S1_THREADS, 2) step1_kernel(Step1Args a) {
   }
   if ((a.phases & S1_DIR) && a.dir_entries > 0) {
     grid_barrier(a.barriers, nbar++, a.status, spin_limit_of(a));
+    const bool use_x8 = a.x8 != nullptr && xdir_x8_pays<true>(a.xm, (uint32_t)a.m, a.dir_entries);
     for (uint32_t b = blockIdx.x * S1_THREADS + threadIdx.x; b < a.dir_entries; b += gridDim.x * S1_THREADS)
-      a.xdir[b] = xdir_entry<true>(a.xm, (uint32_t)a.m, a.dir_shift, b, a.x8 != nullptr);
-    if (a.x8)
-      for (uint32_t i = blockIdx.x * S1_THREADS + threadIdx.x; i < a.m; i += gridDim.x * S1_THREADS)
-        a.x8[i] = xdir_x8<true>(a.xm, a.dir_shift, i);
+      a.xdir[b] = xdir_entry<true>(a.xm, (uint32_t)a.m, a.dir_shift, b, use_x8);
+    if (use_x8)
+      xdir_x8_fill<true>(a.xm, (uint32_t)a.m, a.dir_shift, a.x8, blockIdx.x * S1_THREADS + threadIdx.x,
+                         gridDim.x * S1_THREADS);
   }
 }
 
@@ -1477,10 +1478,10 @@ __global__ void __launch_bounds__(S1_THREADS, merge_blocks_min(W)) step1_merge_k
 // The X_M directory (and its byte table) from the finished X_M.
 __global__ void __launch_bounds__(S1_THREADS) step1_dir_kernel(Step1Args a) {
   const uint32_t t = blockIdx.x * S1_THREADS + threadIdx.x, nt = gridDim.x * S1_THREADS;
+  const bool use_x8 = a.x8 != nullptr && xdir_x8_pays<false>(a.xm, (uint32_t)a.m, a.dir_entries);
   for (uint32_t b = t; b < a.dir_entries; b += nt)
-    a.xdir[b] = xdir_entry<false>(a.xm, (uint32_t)a.m, a.dir_shift, b, a.x8 != nullptr);
-  if (a.x8)
-    for (uint32_t i = t; i < a.m; i += nt) a.x8[i] = xdir_x8<false>(a.xm, a.dir_shift, i);
+    a.xdir[b] = xdir_entry<false>(a.xm, (uint32_t)a.m, a.dir_shift, b, use_x8);
+  if (use_x8) xdir_x8_fill<false>(a.xm, (uint32_t)a.m, a.dir_shift, a.x8, t, nt);
 }
 
 template <int W>
@@ -1671,7 +1672,7 @@ cudaError_t launch_step1_w(Step1Args a, cudaStream_t s, uint32_t sm_count, uint6
                           S1_THREADS, merge_smem_bytes<W>(), s>>>(a);
   ++*launches;
   if ((a.phases & S1_DIR) && a.dir_entries > 0) {
-    const uint64_t work = std::max<uint64_t>(a.dir_entries, a.x8 ? a.m : 0);
+    const uint64_t work = std::max<uint64_t>(a.dir_entries, a.x8 ? (a.m + 3) / 4 : 0);
     step1_dir_kernel<<<(uint32_t)std::min<uint64_t>(4096, (work + S1_THREADS - 1) / S1_THREADS), S1_THREADS, 0, s>>>(a);
     ++*launches;
   }

@@ -67,6 +67,18 @@ __device__ __forceinline__ uint32_t xdir_entry(const uint32_t* __restrict__ xm, 
   return ((2048u - thr) << 20) | (thr == DIR_MANY ? 0u : base);
 }
 
+// Whether the crowded buckets should read the byte table: only when the
+// steps are dense, at least two a bucket on average (their count is X_M's
+// last entry less its code: the new values below the last main value).
+// With fewer, a crowded code's X_M read is the cheaper path, so the buckets
+// are marked DIR_MANY and the table is not written.
+template <bool Coherent>
+__device__ __forceinline__ bool xdir_x8_pays(const uint32_t* __restrict__ xm, uint32_t m, uint32_t entries) {
+  if (m == 0) return false;
+  const uint32_t last = Coherent ? __ldcg(xm + m - 1) : __ldg(xm + m - 1);
+  return (uint64_t)(last - (m - 1)) >= 2ull * entries;
+}
+
 // X8[i] = c[i] - c[first code of i's bucket - 1] (mod 256); read only for
 // codes in buckets marked DIR_MANY8, where it is exact.
 template <bool Coherent>
@@ -75,6 +87,31 @@ __device__ __forceinline__ uint8_t xdir_x8(const uint32_t* __restrict__ xm, uint
   const uint32_t lo = (i >> s) << s;
   const uint32_t base = lo == 0 ? 0u : ld(lo - 1) - (lo - 1);
   return (uint8_t)((ld(i) - i) - base);
+}
+
+// Fills X8 for codes t, t + nt, ... (a grid-stride loop over m codes).  With
+// buckets of at least four codes and aligned tables, one thread takes four
+// consecutive codes of one bucket: a 16-byte load of X_M, one load of the
+// bucket's base and a 4-byte store.
+template <bool Coherent>
+__device__ __forceinline__ void xdir_x8_fill(const uint32_t* __restrict__ xm, uint32_t m, uint32_t s,
+                                             uint8_t* __restrict__ x8, uint32_t t, uint32_t nt) {
+  uint32_t done = 0;
+  if (s >= 2 && (reinterpret_cast<uintptr_t>(xm) & 15u) == 0 && (reinterpret_cast<uintptr_t>(x8) & 3u) == 0) {
+    const uint32_t q = m >> 2;
+    const uint4* xm4 = reinterpret_cast<const uint4*>(xm);
+    uint32_t* x84 = reinterpret_cast<uint32_t*>(x8);
+    for (uint32_t k = t; k < q; k += nt) {
+      const uint32_t i = k << 2, lo = (i >> s) << s;
+      const uint4 v = Coherent ? __ldcg(xm4 + k) : __ldg(xm4 + k);
+      const uint32_t prev = lo == 0 ? 0u : (Coherent ? __ldcg(xm + lo - 1) : __ldg(xm + lo - 1));
+      const uint32_t b = lo == 0 ? i : i + (prev - (lo - 1));   // i + base
+      x84[k] = ((v.x - b) & 0xFFu) | ((v.y - b - 1u) & 0xFFu) << 8 | ((v.z - b - 2u) & 0xFFu) << 16 |
+               (v.w - b - 3u) << 24;
+    }
+    done = q << 2;
+  }
+  for (uint32_t i = done + t; i < m; i += nt) x8[i] = xdir_x8<Coherent>(xm, s, i);
 }
 
 // Bucket shift and entry count of the directory for m main codes.
