@@ -634,14 +634,17 @@ def test_merge_repeats_bulk_copy_ring(ctx, flags):
         assert_parity(ctx, col, f, ref)
 
 
-def test_reencode_byte_table(ctx):
-    """Above 11 * 2^20 main codes the directory's crowded buckets read a byte table of c[i] - base:
-    12M codes with 60k new values (most buckets crowded), plus one insertion point with 300
-    new values (more than a byte holds: that bucket reads X_M)."""
+@pytest.mark.parametrize("n_steps", [60_000, 5_000, 23_137, 23_138])
+def test_reencode_byte_table(ctx, n_steps):
+    """Above 11 * 2^20 main codes the directory's crowded buckets read a byte table of c[i] - base
+    when the steps are dense (two or more a bucket on average), else X_M: 12M codes (11,719
+    buckets of 1024) with 60k new values (most buckets crowded, the table), 5k (a few crowded,
+    X_M), and counts one below and at the rule's 23,438 steps below the last main code; each
+    with one insertion point of 300 new values (more than a byte holds: that bucket reads X_M)."""
     import torch
-    rng = np.random.default_rng(8888)
+    rng = np.random.default_rng(8888 + n_steps)
     m = 12_000_000
-    pts = np.concatenate([rng.integers(0, m + 1, 60_000), np.full(300, 5_000_001)])
+    pts = np.concatenate([rng.integers(0, m + 1, n_steps), np.full(300, 5_000_001)])
     pts.sort()
     xm = (np.arange(m) + np.searchsorted(pts, np.arange(m), side="right")).astype(np.uint32)
     u = m + pts.size
@@ -664,13 +667,16 @@ def test_reencode_byte_table(ctx):
         assert np.array_equal(dm.to_host(out, np.uint32), want), flags
 
 
-def test_merge_column_byte_table(ctx):
-    """A whole merge whose X_M (12M values, 450k new) takes the byte table."""
-    spec = synth.ColumnSpec(n_main=10_000_000, m=12_000_000, w=8, n_delta=1_000_000, f_new=0.5,
-                            dist="zipf", zipf_s=0.8, seed=synth.column_seed(7, 1))
+@pytest.mark.parametrize("n_delta,min_new,max_new", [(1_000_000, 100_000, None), (20_000, 1, 20_000)])
+def test_merge_column_byte_table(ctx, n_delta, min_new, max_new):
+    """Whole merges over 12M main values: with 450k new values X_M's steps are dense and the
+    crowded buckets read the byte table; with a few thousand they read X_M."""
+    spec = synth.ColumnSpec(n_main=10_000_000, m=12_000_000, w=8, n_delta=n_delta, f_new=0.5,
+                            dist="zipf", zipf_s=0.8, seed=synth.column_seed(7, 1 if n_delta >= 1_000_000 else 2))
     col = synth.make_column(spec)
     ref = assert_parity(ctx, col)
-    assert ref.u - col.main_dict.shape[0] > 100_000
+    n_new = ref.u - col.main_dict.shape[0]
+    assert n_new >= min_new and (max_new is None or n_new <= max_new)
 
 
 @pytest.mark.parametrize("b_extra", [0, 1, 4])
