@@ -198,8 +198,10 @@ dm_status dm_merge_dicts(dm_ctx* ctx, uint32_t value_bytes, const void* main_dic
  * from the device scalar *d_bits (which must be <= max_bits; the output
  * buffer holds dm_packed_bytes(n_main + n_delta, max_bits) bytes).  Table
  * entries must be < 2^(*d_bits).  The context's arena holds the lookup
- * structures built on the way when it has room for them: the 64 KiB
- * directory of X_M's steps, then its byte table (m bytes, above 11 * 2^20
+ * structures built on the way when it has room for them: the directory of
+ * X_M's steps (64 KiB; 256 KiB above 2^22 main codes, where its buckets are
+ * refined when shared memory allows, if the arena holds that much), then its
+ * byte table (m bytes, above 11 * 2^20
  * main codes; filled and read only when X_M's steps average two or more a
  * directory bucket) or, above 2^24 main codes, the global directory (8 bytes per 2^s
  * codes, s >= 6, at most 16 MiB); without room X_M is gathered directly. */

@@ -65,7 +65,7 @@ size_t carve_column(void* base, const dm_column_in* in, const dm_column_out* out
   void* slots = c.take(2 * sizeof(void*));
   void* xm = (out && out->x_main) ? nullptr : c.take(m * 4);
   void* xd = (out && out->x_delta) ? nullptr : c.take(d * 4);
-  void* xdir = in->main_rows ? c.take((size_t)dm::reencode_dir_words() * 4) : nullptr;
+  void* xdir = in->main_rows ? c.take((size_t)dm::reencode_dir_words(m) * 4) : nullptr;
   void* x8 = in->main_rows && dm::reencode_wants_x8(m) ? c.take(m) : nullptr;
   const uint64_t gdir_n = in->main_rows ? dm::reencode_gdir_entries(m, d) : 0;
   void* gdir = gdir_n ? c.take(gdir_n * sizeof(uint2)) : nullptr;
@@ -209,6 +209,7 @@ dm::ReencodeArgs plan_args(const dm_column_in* in, const Resolved& r) {
   ra.tune_warps = r.warps;
   ra.tune_stages = r.stages;
   ra.tune_obufs = r.obufs;
+  ra.xdir_words = dm::reencode_dir_words(in->main_dict_len);   // as carve_column lays out
   return ra;
 }
 
@@ -941,8 +942,11 @@ dm_status dm_reencode(dm_ctx* ctx, const uint32_t* main_packed, uint32_t main_bi
   ra.status = ctx->status;
   // the X_M directory goes to the arena when it has room (else no
   // directory), its byte table after it when that fits too
-  const size_t dir_bytes = (size_t)dm::reencode_dir_words() * 4;
+  // (the refined directory's room when the arena has it, else the unrefined)
+  size_t dir_bytes = (size_t)dm::reencode_dir_words(m) * 4;
+  if (ctx->arena_bytes < dir_bytes) dir_bytes = (size_t)dm::reencode_dir_words(0) * 4;
   ra.xdir = ctx->arena_bytes >= dir_bytes ? static_cast<uint32_t*>(ctx->arena) : nullptr;
+  ra.xdir_words = (uint32_t)(dir_bytes / 4);
   ra.x8 = ra.xdir && dm::reencode_wants_x8(m) && ctx->arena_bytes >= dir_bytes + m
               ? static_cast<uint8_t*>(ctx->arena) + dir_bytes
               : nullptr;

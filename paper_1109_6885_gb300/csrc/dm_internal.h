@@ -105,7 +105,8 @@ struct ReencodeArgs {
   uint32_t max_bits;         // host bound of E'_C; sizes the output buffer
   uint32_t* out_words;
   uint32_t* status;
-  uint32_t* xdir;            // scratch for the X_M directory (reencode_dir_words() words) or NULL
+  uint32_t* xdir;            // scratch for the X_M directory or NULL
+  uint32_t xdir_words;       // words at xdir (0: reencode_dir_words(0), the unrefined maximum)
   uint8_t* x8;               // scratch for its byte table ([m]) or NULL
   uint2* gdir;               // scratch for the global directory (reencode_gdir_entries(m, d)) or NULL
   uint32_t tune_warps;       // 0 = default; warps per block
@@ -113,7 +114,9 @@ struct ReencodeArgs {
   uint32_t tune_obufs;       // 0 = default; output buffers per warp
 };
 
-uint32_t reencode_dir_words();
+// Words of directory scratch a column of m main codes is given: room for the
+// refined directory above 2^22 main codes, else the unrefined maximum.
+uint32_t reencode_dir_words(uint64_t m);
 // Most main codes a directory can cover (m above it: no directory, no byte table).
 uint64_t reencode_dir_max_codes();
 // Whether a column of m main codes gets the directory's byte table.

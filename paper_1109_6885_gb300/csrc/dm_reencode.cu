@@ -558,7 +558,7 @@ Registry& registry() {
 
 }  // namespace
 
-uint32_t reencode_dir_words() { return RE_DIR_MAX; }
+uint32_t reencode_dir_words(uint64_t m) { return m > RE_DIR_FINE_MIN_CODES ? RE_DIR_FINE_MAX : RE_DIR_MAX; }
 uint64_t reencode_dir_max_codes() { return (uint64_t)RE_DIR_MAX << RE_DIR_SHIFT_MAX; }
 bool reencode_wants_x8(uint64_t m) { return m > RE_X8_MIN_CODES && m <= reencode_dir_max_codes(); }
 
@@ -583,6 +583,12 @@ struct ReencodePlanImpl {
   KernelFn fn;
 };
 static_assert(sizeof(ReencodePlanImpl) <= sizeof(ReencodePlan), "plan storage");
+
+// Default warps a block of a column whose directory is refined.
+constexpr uint32_t RE_WARPS_FINE = 12;
+// Shared memory of a block with a refined directory at most: the 196 KB
+// carve-out level, which leaves 60 KB of the SM's 256 KB to L1.
+constexpr uint32_t RE_SMEM_KEEP_L1 = 196u << 10;
 
 cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, uint32_t flags, ReencodePlan* out) {
   if (b > 32 || a.max_bits > 32) return cudaErrorInvalidValue;
@@ -623,7 +629,13 @@ cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, 
     uint64_t w = fixed < (uint64_t)optin ? ((uint64_t)optin - fixed) / per : 0;
     return (uint32_t)(w < cap ? w : cap);
   };
-  const uint32_t want_warps = a.tune_warps >= 1 && a.tune_warps <= RE_WARPS_MAX ? a.tune_warps : 16;
+  // (12 by default for directory columns of 2^22 to 11 * 2^20 main codes,
+  // whose freed staging refines the directory below: Step 2(b) of a 10M-value
+  // column with 30k new values took 0.233 ms against 0.348 at 16 warps, and
+  // 0.143 against 0.135 with 3k)
+  const bool fine = L.x_mode == 2 && a.m > RE_DIR_FINE_MIN_CODES && a.m <= RE_X8_MIN_CODES;
+  const uint32_t want_warps =
+      a.tune_warps >= 1 && a.tune_warps <= RE_WARPS_MAX ? a.tune_warps : (fine ? RE_WARPS_FINE : 16u);
   P.warps = fit(L, want_warps);
   if ((L.x_mode == 1 || L.x_mode == 2) && P.warps < 4) {
     L.x_mode = 0;
@@ -632,6 +644,26 @@ cudaError_t plan_reencode(uint32_t b, const ReencodeArgs& a, uint32_t sm_count, 
     P.warps = fit(L, want_warps);
   }
   if (P.warps < 1) return cudaErrorInvalidConfiguration;
+  // Above 2^22 main codes X_M is far larger than L1, so a code in a bucket
+  // with several steps costs an L2 gather.  Buckets are halved while the
+  // finer directory fits the scratch, leaves the block as many warps and
+  // keeps its shared memory within RE_SMEM_KEEP_L1 (the L1 left beside it
+  // holds the gathers in flight; a block of 227 KB halves it and slowed a
+  // step-dense column's Step 2(b) from 0.47 to 0.87 ms).  With 16 warps the
+  // rule leaves the directory as it is; fewer warps trade their staging
+  // for finer buckets.
+  if (L.x_mode == 2 && a.m > RE_DIR_FINE_MIN_CODES) {
+    const uint32_t words = a.xdir_words ? a.xdir_words : RE_DIR_MAX;
+    while (L.dir_shift > 0) {
+      Layout l2 = L;
+      l2.dir_shift = L.dir_shift - 1;
+      const uint64_t n = ((uint64_t)a.m + (1ull << l2.dir_shift) - 1) >> l2.dir_shift;
+      if (n > words) break;
+      l2.x_entries = (uint32_t)n;
+      if (fit(l2, want_warps) < P.warps || smem_bytes(l2, P.warps) > RE_SMEM_KEEP_L1) break;
+      L = l2;
+    }
+  }
   P.bytes = smem_bytes(L, P.warps);
   Registry& R = registry();
   P.fn = R.fn[b];

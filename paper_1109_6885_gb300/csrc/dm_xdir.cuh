@@ -36,6 +36,11 @@ static_assert((DIR_MANY_TOP << 20) < DIR_SLOW_BELOW && (DIR_MANY8_TOP << 20) < D
               "markers");
 constexpr uint32_t RE_DIR_MAX = 16384;               // entries (64 KiB of shared memory)
 constexpr uint32_t RE_DIR_SHIFT_MAX = 10;
+// A refined directory (finer buckets than xdir_shape's, where shared memory
+// allows) for more than RE_DIR_FINE_MIN_CODES main codes: at most this many
+// entries of scratch.
+constexpr uint32_t RE_DIR_FINE_MAX = 65536;
+constexpr uint64_t RE_DIR_FINE_MIN_CODES = 1ull << 22;
 static_assert((1u << RE_DIR_SHIFT_MAX) <= DIR_NONE, "a bucket without steps never carries");
 
 // Entry of bucket b.  Coherent: X_M was written earlier in the same kernel,

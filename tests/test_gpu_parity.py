@@ -618,6 +618,24 @@ def test_tuning_changes_nothing(warps, stages, obufs):
     c.close()
 
 
+@pytest.mark.parametrize("m,warps", [(5_000_000, 12), (5_000_000, 8), (10_000_000, 10), (10_000_000, 8)])
+def test_refined_directory(m, warps):
+    """Above 2^22 main codes a block with fewer warps gives its freed shared memory to finer
+    directory buckets (halved while the block stays within 196 KB): 5M codes at 23 bits take
+    256-code buckets instead of 512, 10M codes at 24 bits 512 instead of 1024.  The delta
+    leaves buckets without steps, with one step and with several."""
+    from paper_1109_6885_gb300 import build
+    build.build()
+    c = dm.Context(0, 64 << 20)
+    c.set_tuning(reencode_warps=warps)
+    spec = synth.ColumnSpec(n_main=3_000_007, m=m, w=8, n_delta=400_000, f_new=0.3, dist="zipf",
+                            zipf_s=0.8, seed=synth.column_seed(17, m // 1_000_000 + warps))
+    col = synth.make_column(spec)
+    ref = assert_parity(c, col)
+    assert ref.u > m
+    c.close()
+
+
 @pytest.mark.parametrize("flags", [0, "X_GLOBAL", "X_SMEM"])
 def test_merge_repeats_bulk_copy_ring(ctx, flags):
     """A column whose re-encode once read a bulk-copy stage while the copy refilling it
